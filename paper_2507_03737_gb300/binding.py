@@ -1,0 +1,279 @@
+"""ctypes binding of ``libs3gs.so`` (C ABI in ``include/s3gs.h``).
+
+Argument marshalling only: every computation runs in the CUDA library. The
+functions keep the C names; tensors are passed as device pointers and the
+current torch CUDA stream is used unless one is given. There is no fallback:
+if the library is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "S3GS_OK", "S3GS_E_INVALID", "S3GS_E_CAPACITY", "S3GS_E_CUDA", "S3GS_E_TIMEOUT",
+    "S3GS_E_NOMEM", "S3GS_E_STATE", "S3GS_MAX_VIEWS", "S3GSError", "Gaussians", "Camera",
+    "Options", "lib", "s3gs_options_default", "s3gs_create", "s3gs_destroy", "s3gs_last_error",
+    "s3gs_state_create", "s3gs_state_destroy", "s3gs_reserve", "s3gs_render_fwd",
+    "s3gs_render_bwd", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_debug_records",
+    "s3gs_debug_binning", "s3gs_set_counting", "s3gs_read_counters", "s3gs_version",
+    "s3gs_set_timing", "s3gs_read_timing", "STAGES",
+    "make_cameras", "make_gaussians", "check",
+]
+
+S3GS_OK, S3GS_E_INVALID, S3GS_E_CAPACITY, S3GS_E_CUDA = 0, -1, -2, -3
+S3GS_E_TIMEOUT, S3GS_E_NOMEM, S3GS_E_STATE = -4, -5, -6
+S3GS_MAX_VIEWS = 32
+_NAMES = {0: "OK", -1: "INVALID", -2: "CAPACITY", -3: "CUDA", -4: "TIMEOUT", -5: "NOMEM", -6: "STATE"}
+
+
+class S3GSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"s3gs {_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
+                ("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
+                ("colors", ctypes.c_void_p)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("T_cw", ctypes.c_float * 12)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32), ("recompute", ctypes.c_int32),
+                ("auto_grow", ctypes.c_int32), ("near_z", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+_P = ctypes.c_void_p
+_lib = None
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libs3gs.so is not built ({path}); run __graft_entry__.build() or "
+                          "python -m paper_2507_03737_gb300.build")
+    L = ctypes.CDLL(path)
+    sig = {
+        "s3gs_options_default": (None, [ctypes.POINTER(Options)]),
+        "s3gs_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P)]),
+        "s3gs_destroy": (None, [_P]),
+        "s3gs_last_error": (ctypes.c_char_p, [_P]),
+        "s3gs_state_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+        "s3gs_state_destroy": (None, [_P]),
+        "s3gs_reserve": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_int64]),
+        "s3gs_render_fwd": (ctypes.c_int, [_P, _P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera),
+                                           ctypes.c_int32, _P, ctypes.POINTER(Options), _P, _P, _P, _P, _P]),
+        "s3gs_render_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                           ctypes.c_int32, _P]),
+        "s3gs_state_check": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]),
+        "s3gs_mapping_loss": (ctypes.c_int, [_P, ctypes.POINTER(Camera), ctypes.c_int32, _P, _P, _P, _P, _P,
+                                             _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                             _P, _P, _P, _P, _P]),
+        "s3gs_debug_records": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+        "s3gs_debug_binning": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64)]),
+        "s3gs_set_counting": (ctypes.c_int, [_P, ctypes.c_int32]),
+        "s3gs_read_counters": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "s3gs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+        "s3gs_read_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+        "s3gs_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or t.dtype != torch.float32 and t.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("expected a float32 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def check(ctx, status):
+    if status != S3GS_OK:
+        msg = lib().s3gs_last_error(ctx).decode() if ctx else ""
+        raise S3GSError(status, msg)
+
+
+def s3gs_version() -> str:
+    return lib().s3gs_version().decode()
+
+
+def s3gs_options_default(**kw) -> Options:
+    o = Options()
+    lib().s3gs_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "bg":
+            for i in range(3):
+                o.bg[i] = float(v[i])
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def s3gs_create(device: int = 0):
+    h = _P()
+    st = lib().s3gs_create(int(device), ctypes.byref(h))
+    if st != S3GS_OK:
+        raise S3GSError(st, f"cannot create a context on device {device}")
+    return h.value
+
+
+def s3gs_destroy(ctx):
+    lib().s3gs_destroy(ctx)
+
+
+def s3gs_last_error(ctx) -> str:
+    return lib().s3gs_last_error(ctx).decode()
+
+
+def s3gs_state_create(ctx):
+    h = _P()
+    check(ctx, lib().s3gs_state_create(ctx, ctypes.byref(h)))
+    return h.value
+
+
+def s3gs_state_destroy(state):
+    lib().s3gs_state_destroy(state)
+
+
+def s3gs_reserve(ctx, state, n, n_views, total_pixels, total_tiles, max_duplicates):
+    check(ctx, lib().s3gs_reserve(ctx, state, int(n), int(n_views), int(total_pixels),
+                                  int(total_tiles), int(max_duplicates)))
+
+
+def make_gaussians(means, log_scales, quats, opacity_logits, colors, sh_degree) -> Gaussians:
+    n = int(means.shape[0])
+    return Gaussians(n, int(sh_degree), _ptr(means), _ptr(log_scales), _ptr(quats),
+                     _ptr(opacity_logits), _ptr(colors))
+
+
+def make_cameras(cameras):
+    """cameras: list of dicts (width, height, fx, fy, cx, cy, T_cw 3x4)."""
+    arr = (Camera * len(cameras))()
+    for k, c in enumerate(cameras):
+        arr[k].width, arr[k].height = int(c["width"]), int(c["height"])
+        arr[k].fx, arr[k].fy, arr[k].cx, arr[k].cy = (float(c["fx"]), float(c["fy"]),
+                                                       float(c["cx"]), float(c["cy"]))
+        T = [float(x) for x in __import__("numpy").asarray(c["T_cw"], dtype="float64").reshape(12)]
+        for i in range(12):
+            arr[k].T_cw[i] = T[i]
+    return arr
+
+
+def s3gs_render_fwd(ctx, state, gaussians: Gaussians, cams, n_views, T_cw_device, options: Options,
+                    rgb, depth, pointmap, alpha, stream=None):
+    check(ctx, lib().s3gs_render_fwd(ctx, state, ctypes.byref(gaussians), cams, int(n_views),
+                                     _ptr(T_cw_device), ctypes.byref(options), _ptr(rgb), _ptr(depth),
+                                     _ptr(pointmap), _ptr(alpha), _stream(stream)))
+
+
+def s3gs_render_bwd(ctx, state, d_rgb, d_depth, d_pointmap, d_alpha, d_means, d_log_scales, d_quats,
+                    d_opacity_logits, d_colors, d_twist, accumulate=0, stream=None):
+    check(ctx, lib().s3gs_render_bwd(ctx, state, _ptr(d_rgb), _ptr(d_depth), _ptr(d_pointmap),
+                                     _ptr(d_alpha), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats),
+                                     _ptr(d_opacity_logits), _ptr(d_colors), _ptr(d_twist),
+                                     int(accumulate), _stream(stream)))
+
+
+def s3gs_state_check(ctx, state, raise_on_error=True):
+    k = ctypes.c_int64(); cap = ctypes.c_int64()
+    st = lib().s3gs_state_check(ctx, state, ctypes.byref(k), ctypes.byref(cap))
+    if raise_on_error:
+        check(ctx, st)
+    return st, k.value, cap.value
+
+
+def s3gs_mapping_loss(ctx, cams, n_views, rgb, depth, pointmap, t_rgb, t_depth, t_pointmap, mask,
+                      w_rgb, w_depth, w_geo, d_rgb, d_depth, d_pointmap, loss_device, stream=None):
+    check(ctx, lib().s3gs_mapping_loss(ctx, cams, int(n_views), _ptr(rgb), _ptr(depth), _ptr(pointmap),
+                                       _ptr(t_rgb), _ptr(t_depth), _ptr(t_pointmap), _ptr(mask),
+                                       float(w_rgb), float(w_depth), float(w_geo), _ptr(d_rgb),
+                                       _ptr(d_depth), _ptr(d_pointmap), _ptr(loss_device),
+                                       _stream(stream)))
+
+
+def s3gs_debug_records(ctx, state, n_records):
+    import numpy as np
+    xy = np.zeros((n_records, 2), np.float32); co = np.zeros((n_records, 4), np.float32)
+    rz = np.zeros((n_records, 4), np.float32); ext = np.zeros((n_records, 2), np.int32)
+    check(ctx, lib().s3gs_debug_records(ctx, state, int(n_records), xy.ctypes.data, co.ctypes.data,
+                                        rz.ctypes.data, ext.ctypes.data))
+    return dict(xy=xy, conic_opacity=co, rgb_depth=rz, extent=ext)
+
+
+def s3gs_debug_binning(ctx, state):
+    import numpy as np
+    nt = ctypes.c_int64(); nk = ctypes.c_int64()
+    check(ctx, lib().s3gs_debug_binning(ctx, state, None, None, None, ctypes.byref(nt), ctypes.byref(nk)))
+    keys = np.zeros(max(nk.value, 1), np.uint64); vals = np.zeros(max(nk.value, 1), np.uint32)
+    ranges = np.zeros(nt.value + 1, np.int64)
+    check(ctx, lib().s3gs_debug_binning(ctx, state, keys.ctypes.data, vals.ctypes.data, ranges.ctypes.data,
+                                        ctypes.byref(nt), ctypes.byref(nk)))
+    return keys[:nk.value], vals[:nk.value], ranges
+
+
+STAGES = ("project", "scan", "emit", "tile_sort", "tile_order", "blend_fwd", "blend_bwd", "det_reduce",
+          "project_bwd", "twist_reduce", "loss")
+
+
+def s3gs_set_timing(ctx, enable: bool):
+    check(ctx, lib().s3gs_set_timing(ctx, int(bool(enable))))
+
+
+def s3gs_read_timing(ctx) -> dict:
+    arr = (ctypes.c_float * len(STAGES))()
+    check(ctx, lib().s3gs_read_timing(ctx, arr, len(STAGES)))
+    return {k: float(arr[i]) for i, k in enumerate(STAGES) if arr[i] >= 0}
+
+
+def s3gs_set_counting(ctx, enable: bool):
+    check(ctx, lib().s3gs_set_counting(ctx, int(bool(enable))))
+
+
+def s3gs_read_counters(ctx, state):
+    a = ctypes.c_int64(); b = ctypes.c_int64(); c = ctypes.c_int64()
+    check(ctx, lib().s3gs_read_counters(ctx, state, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(fwd_processed=a.value, fwd_blended=b.value, bwd_processed=c.value)

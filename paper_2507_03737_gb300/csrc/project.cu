@@ -1,0 +1,504 @@
+// EWA projection of 3D Gaussians (Sec. 3.1, Eq. 1) and its backward (Sec. 3.2.2,
+// Eq. 11), as structure-of-arrays passes with one thread per Gaussian looping
+// over all views of the call, so each Gaussian's parameters are read once per
+// call however many views there are.
+#include "s3gs_internal.cuh"
+
+namespace s3gs {
+namespace {
+
+// Real orthonormal spherical harmonics (no Condon-Shortley phase), l = 1..3,
+// at a unit direction; coefficient k = l^2 + l + m. Constants are
+// sqrt((2l+1)/(4 pi) * (l-|m|)!/(l+|m|)!) times the polynomial normalisation.
+constexpr float kSH1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+constexpr float kSH2a = 1.09254843059207907f;  // 0.5 sqrt(15 / pi)
+constexpr float kSH2b = 0.31539156525252001f;  // 0.25 sqrt(5 / pi)
+constexpr float kSH2c = 0.54627421529603954f;  // 0.25 sqrt(15 / pi)
+constexpr float kSH3a = 0.59004358992664352f;  // 0.25 sqrt(35 / (2 pi))
+constexpr float kSH3b = 2.89061144264055406f;  // 0.5 sqrt(105 / pi)
+constexpr float kSH3c = 0.45704579946446573f;  // 0.25 sqrt(21 / (2 pi))
+constexpr float kSH3d = 0.37317633259011540f;  // 0.25 sqrt(7 / pi)
+constexpr float kSH3e = 1.44530572132027703f;  // 0.25 sqrt(105 / pi)
+
+template <int D>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
+    Y[0] = 1.0f;  // the DC coefficient is used directly (Eq. 2 colour)
+    if (D >= 1) {
+        Y[1] = kSH1 * y;
+        Y[2] = kSH1 * z;
+        Y[3] = kSH1 * x;
+    }
+    if (D >= 2) {
+        Y[4] = kSH2a * x * y;
+        Y[5] = kSH2a * y * z;
+        Y[6] = kSH2b * (3.0f * z * z - 1.0f);
+        Y[7] = kSH2a * x * z;
+        Y[8] = kSH2c * (x * x - y * y);
+    }
+    if (D >= 3) {
+        Y[9] = kSH3a * y * (3.0f * x * x - y * y);
+        Y[10] = kSH3b * x * y * z;
+        Y[11] = kSH3c * y * (5.0f * z * z - 1.0f);
+        Y[12] = kSH3d * z * (5.0f * z * z - 3.0f);
+        Y[13] = kSH3c * x * (5.0f * z * z - 1.0f);
+        Y[14] = kSH3e * z * (x * x - y * y);
+        Y[15] = kSH3a * x * (x * x - 3.0f * y * y);
+    }
+}
+
+// sum_k w[k] * grad Y_k (gradient of the polynomials above in x, y, z)
+template <int D>
+__device__ __forceinline__ float3 sh_weighted_grad(float x, float y, float z, const float w[16]) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (D >= 1) {
+        gy += kSH1 * w[1];
+        gz += kSH1 * w[2];
+        gx += kSH1 * w[3];
+    }
+    if (D >= 2) {
+        gx += kSH2a * y * w[4];  gy += kSH2a * x * w[4];
+        gy += kSH2a * z * w[5];  gz += kSH2a * y * w[5];
+        gz += kSH2b * 6.0f * z * w[6];
+        gx += kSH2a * z * w[7];  gz += kSH2a * x * w[7];
+        gx += kSH2c * 2.0f * x * w[8];  gy -= kSH2c * 2.0f * y * w[8];
+    }
+    if (D >= 3) {
+        gx += kSH3a * 6.0f * x * y * w[9];
+        gy += kSH3a * (3.0f * x * x - 3.0f * y * y) * w[9];
+        gx += kSH3b * y * z * w[10]; gy += kSH3b * x * z * w[10]; gz += kSH3b * x * y * w[10];
+        gy += kSH3c * (5.0f * z * z - 1.0f) * w[11]; gz += kSH3c * 10.0f * y * z * w[11];
+        gz += kSH3d * (15.0f * z * z - 3.0f) * w[12];
+        gx += kSH3c * (5.0f * z * z - 1.0f) * w[13]; gz += kSH3c * 10.0f * x * z * w[13];
+        gx += kSH3e * 2.0f * x * z * w[14]; gy -= kSH3e * 2.0f * y * z * w[14];
+        gz += kSH3e * (x * x - y * y) * w[14];
+        gx += kSH3a * (3.0f * x * x - 3.0f * y * y) * w[15];
+        gy -= kSH3a * 6.0f * x * y * w[15];
+    }
+    return make_float3(gx, gy, gz);
+}
+
+struct Activated {
+    float s[3];
+    float qn[4];
+    float qinv;   // 1 / |q|
+    float R[9];
+    float Sig[6]; // world covariance: xx, xy, xz, yy, yz, zz
+    float opacity;
+};
+
+__device__ __forceinline__ bool activate(const float *ls, const float *q, float ol, Activated &A) {
+    A.s[0] = expf(ls[0]);
+    A.s[1] = expf(ls[1]);
+    A.s[2] = expf(ls[2]);
+    float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (!(qq > 0.f)) return false;
+    float nrm = sqrtf(qq);
+    A.qinv = 1.0f / nrm;
+    float w = q[0] * A.qinv, x = q[1] * A.qinv, y = q[2] * A.qinv, z = q[3] * A.qinv;
+    A.qn[0] = w; A.qn[1] = x; A.qn[2] = y; A.qn[3] = z;
+    float *R = A.R;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+    // Sigma = (R S)(R S)^T
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * A.s[j];
+    A.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    A.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    A.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    A.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    A.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    A.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    A.opacity = 1.0f / (1.0f + expf(-ol));
+    return true;
+}
+
+__device__ __forceinline__ void sym_full(const float s[6], float F[9]) {
+    F[0] = s[0]; F[1] = s[1]; F[2] = s[2];
+    F[3] = s[1]; F[4] = s[3]; F[5] = s[4];
+    F[6] = s[2]; F[7] = s[4]; F[8] = s[5];
+}
+
+// Camera-frame covariance Sc = W Sig W^T (full 3x3).
+__device__ __forceinline__ void cam_cov(const float T[12], const float Sig[6], float Sc[9]) {
+    float S[9], WS[9];
+    sym_full(Sig, S);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            WS[3 * i + j] = T[4 * i] * S[j] + T[4 * i + 1] * S[3 + j] + T[4 * i + 2] * S[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Sc[3 * i + j] = WS[3 * i] * T[4 * j] + WS[3 * i + 1] * T[4 * j + 1] + WS[3 * i + 2] * T[4 * j + 2];
+}
+
+__device__ __forceinline__ void cam_centre(const float T[12], float c[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] = -(T[i] * T[3] + T[4 + i] * T[7] + T[8 + i] * T[11]);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const __grid_constant__ ViewBatch vb) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    constexpr int NC = (D + 1) * (D + 1);
+    float m[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
+    float ls[3] = {a.log_scales[3 * g], a.log_scales[3 * g + 1], a.log_scales[3 * g + 2]};
+    float4 q4 = reinterpret_cast<const float4 *>(a.quats)[g];
+    float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    Activated A;
+    bool ok = activate(ls, q, a.opacity_logits[g], A);
+    float k[NC * 3];
+    const float *cp = a.colors + (long long)g * NC * 3;
+#pragma unroll
+    for (int i = 0; i < NC * 3; ++i) k[i] = cp[i];
+
+    for (int v = 0; v < vb.n_views; ++v) {
+        const ViewInfo &vi = vb.v[v];
+        long long r = (long long)v * a.n + g;
+        int2 ext = make_int2(0, 0);
+        float T[12];
+        load_pose(vi, a.Tdev, v, T);
+        float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
+        float py = T[4] * m[0] + T[5] * m[1] + T[6] * m[2] + T[7];
+        float pz = T[8] * m[0] + T[9] * m[1] + T[10] * m[2] + T[11];
+        if (ok && pz > a.near_z) {
+            float Sc[9];
+            cam_cov(T, A.Sig, Sc);
+            float iz = 1.0f / pz;
+            float j00 = vi.fx * iz, j02 = -vi.fx * px * iz * iz;
+            float j11 = vi.fy * iz, j12 = -vi.fy * py * iz * iz;
+            // cov2 = J Sc J^T + 0.3 I, J = [[j00, 0, j02], [0, j11, j12]]
+            float ca = j00 * (j00 * Sc[0] + j02 * Sc[2]) + j02 * (j00 * Sc[6] + j02 * Sc[8]) + kDilation;
+            float cb = j11 * (j00 * Sc[1] + j02 * Sc[7]) + j12 * (j00 * Sc[2] + j02 * Sc[8]);
+            float cc = j11 * (j11 * Sc[4] + j12 * Sc[5]) + j12 * (j11 * Sc[7] + j12 * Sc[8]) + kDilation;
+            float det = ca * cc - cb * cb;
+            float u = vi.fx * px * iz + vi.cx;
+            float vv = vi.fy * py * iz + vi.cy;
+            if (det > 0.f && isfinite(u) && isfinite(vv)) {
+                float idet = 1.0f / det;
+                // integer half-extents of the 3-sigma ellipse's bounding box
+                float ex = ceilf(3.0f * sqrtf(ca)), ey = ceilf(3.0f * sqrtf(cc));
+                int rx = ex < (float)kExtentMax ? (int)ex : kExtentMax;
+                int ry = ey < (float)kExtentMax ? (int)ey : kExtentMax;
+                float x0 = ceilf(__fsub_rn(u, (float)rx)), x1 = floorf(__fadd_rn(u, (float)rx));
+                float y0 = ceilf(__fsub_rn(vv, (float)ry)), y1 = floorf(__fadd_rn(vv, (float)ry));
+                if (x1 >= 0.f && x0 <= (float)(vi.w - 1) && y1 >= 0.f && y0 <= (float)(vi.h - 1) && x0 <= x1 && y0 <= y1) {
+                    int tx0 = (x0 > 0.f ? (int)x0 : 0) / vb.tile_w;
+                    int tx1 = (x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1) / vb.tile_w;
+                    int ty0 = (y0 > 0.f ? (int)y0 : 0) / vb.tile_h;
+                    int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
+                    // colour (Eq. 2; SH for degree >= 1)
+                    float col[3];
+                    if (D == 0) {
+                        col[0] = k[0]; col[1] = k[1]; col[2] = k[2];
+                    } else {
+                        float C[3];
+                        cam_centre(T, C);
+                        float dx = m[0] - C[0], dy = m[1] - C[1], dz = m[2] - C[2];
+                        float in = rsqrtf(dx * dx + dy * dy + dz * dz);
+                        float Y[16];
+                        sh_basis<D>(dx * in, dy * in, dz * in, Y);
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            float c = k[ch];
+#pragma unroll
+                            for (int i = 1; i < NC; ++i) c += Y[i] * k[3 * i + ch];
+                            col[ch] = fmaxf(c, 0.0f);
+                        }
+                    }
+                    Record R;
+                    R.a = make_float4(u, vv, cc * idet, -cb * idet);
+                    R.b = make_float4(ca * idet, A.opacity, pz, 0.f);
+                    R.c = make_float4(col[0], col[1], col[2], 0.f);
+                    a.rec[r] = R;
+                    ext = make_int2(rx, ry);
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx)
+                            atomicAdd(a.tile_count + vi.tile_base + ty * vi.tiles_x + tx, 1u);
+                }
+            }
+        }
+        a.ext[r] = ext;
+    }
+}
+
+// Backward of the projection for every view of one Gaussian, accumulating
+// the parameter gradients in registers and writing each once.
+template <int D>
+__global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a, const __grid_constant__ ViewBatch vb) {
+    constexpr int NC = (D + 1) * (D + 1);
+    __shared__ float s_tw[8][S3GS_MAX_VIEWS][6];
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool live = g < a.n;
+    long long gg = live ? g : 0;
+
+    float m[3] = {a.means[3 * gg], a.means[3 * gg + 1], a.means[3 * gg + 2]};
+    float ls[3] = {a.log_scales[3 * gg], a.log_scales[3 * gg + 1], a.log_scales[3 * gg + 2]};
+    float4 q4 = reinterpret_cast<const float4 *>(a.quats)[gg];
+    float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    Activated A;
+    bool ok = activate(ls, q, a.opacity_logits[gg], A) && live;
+    float k[NC * 3];
+    const float *cp = a.colors + gg * NC * 3;
+#pragma unroll
+    for (int i = 0; i < NC * 3; ++i) k[i] = cp[i];
+
+    float dmu[3] = {0.f, 0.f, 0.f};
+    float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // gradient w.r.t. the world covariance
+    float dO = 0.f;
+    float dk[NC * 3];
+#pragma unroll
+    for (int i = 0; i < NC * 3; ++i) dk[i] = 0.f;
+
+    for (int v = 0; v < vb.n_views; ++v) {
+        const ViewInfo &vi = vb.v[v];
+        long long r = (long long)v * a.n + gg;
+        float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int2 ext = ok ? a.ext[r] : make_int2(0, 0);
+        if (ext.x > 0) {
+            float gr[kGrad2d];
+            float *gp = a.grad2d + r * kGrad2d;
+#pragma unroll
+            for (int i = 0; i < kGrad2d; ++i) gr[i] = gp[i];
+#pragma unroll
+            for (int i = 0; i < kGrad2d; ++i) gp[i] = 0.f;  // leave the accumulator clean
+            float T[12];
+            load_pose(vi, a.Tdev, v, T);
+            float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
+            float py = T[4] * m[0] + T[5] * m[1] + T[6] * m[2] + T[7];
+            float pz = T[8] * m[0] + T[9] * m[1] + T[10] * m[2] + T[11];
+            float Sc[9];
+            cam_cov(T, A.Sig, Sc);
+            float iz = 1.0f / pz, iz2 = iz * iz;
+            float fx = vi.fx, fy = vi.fy;
+            float j00 = fx * iz, j02 = -fx * px * iz2, j11 = fy * iz, j12 = -fy * py * iz2;
+            float ca = j00 * (j00 * Sc[0] + j02 * Sc[2]) + j02 * (j00 * Sc[6] + j02 * Sc[8]) + kDilation;
+            float cb = j11 * (j00 * Sc[1] + j02 * Sc[7]) + j12 * (j00 * Sc[2] + j02 * Sc[8]);
+            float cc = j11 * (j11 * Sc[4] + j12 * Sc[5]) + j12 * (j11 * Sc[7] + j12 * Sc[8]) + kDilation;
+            float idet = 1.0f / (ca * cc - cb * cb);
+            float cA = cc * idet, cB = -cb * idet, cC = ca * idet;
+            // conic -> 2D covariance: G2 = -Sinv Ginv Sinv, Ginv = [[gA, gB/2], [gB/2, gC]]
+            float hB = 0.5f * gr[kGB];
+            float t00 = cA * gr[kGA] + cB * hB, t01 = cA * hB + cB * gr[kGC];
+            float t10 = cB * gr[kGA] + cC * hB, t11 = cB * hB + cC * gr[kGC];
+            float g00 = -(t00 * cA + t01 * cB);
+            float g01 = -(t00 * cB + t01 * cC);
+            float g11 = -(t10 * cB + t11 * cC);
+            // cov2 = J Sc J^T: dSc = J^T G2 J, dJ = 2 G2 J Sc
+            float P0[3] = {g00 * j00, g01 * j11, g00 * j02 + g01 * j12};  // row 0 of G2 J
+            float P1[3] = {g01 * j00, g11 * j11, g01 * j02 + g11 * j12};  // row 1 of G2 J
+            float Gc[9];
+            const float J0[3] = {j00, 0.f, j02}, J1[3] = {0.f, j11, j12};
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) Gc[3 * i + j] = J0[i] * P0[j] + J1[i] * P1[j];
+            float dJ00 = 2.f * (P0[0] * Sc[0] + P0[1] * Sc[3] + P0[2] * Sc[6]);
+            float dJ02 = 2.f * (P0[0] * Sc[2] + P0[1] * Sc[5] + P0[2] * Sc[8]);
+            float dJ11 = 2.f * (P1[0] * Sc[1] + P1[1] * Sc[4] + P1[2] * Sc[7]);
+            float dJ12 = 2.f * (P1[0] * Sc[2] + P1[1] * Sc[5] + P1[2] * Sc[8]);
+            // Sc = W Sig W^T: dSig += W^T Gc W
+            float GW[9];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    GW[3 * i + j] = Gc[3 * i] * T[j] + Gc[3 * i + 1] * T[4 + j] + Gc[3 * i + 2] * T[8 + j];
+            {
+                float WG[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        WG[3 * i + j] = T[i] * GW[j] + T[4 + i] * GW[3 + j] + T[8 + i] * GW[6 + j];
+                dSig[0] += WG[0]; dSig[1] += WG[1]; dSig[2] += WG[2];
+                dSig[3] += WG[4]; dSig[4] += WG[5]; dSig[5] += WG[8];
+            }
+            // camera-frame mean
+            float dp0 = gr[kGU] * fx * iz - dJ02 * fx * iz2;
+            float dp1 = gr[kGV] * fy * iz - dJ12 * fy * iz2;
+            float dp2 = -gr[kGU] * fx * px * iz2 - gr[kGV] * fy * py * iz2 + gr[kGZ] - dJ00 * fx * iz2 +
+                        2.f * dJ02 * fx * px * iz2 * iz - dJ11 * fy * iz2 + 2.f * dJ12 * fy * py * iz2 * iz;
+            dmu[0] += T[0] * dp0 + T[4] * dp1 + T[8] * dp2;
+            dmu[1] += T[1] * dp0 + T[5] * dp1 + T[9] * dp2;
+            dmu[2] += T[2] * dp0 + T[6] * dp1 + T[10] * dp2;
+            // twist: dp = rho + phi x p; dSc = [phi]x Sc - Sc [phi]x
+            tw[0] = dp0; tw[1] = dp1; tw[2] = dp2;
+            tw[3] = py * dp2 - pz * dp1;
+            tw[4] = pz * dp0 - px * dp2;
+            tw[5] = px * dp1 - py * dp0;
+            // Q = Sc Gc - Gc Sc; dphi += 2 (Q12, Q20, Q01)
+            float Q12 = 0.f, Q20 = 0.f, Q01 = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                Q12 += Sc[3 + kk] * Gc[3 * kk + 2] - Gc[3 + kk] * Sc[3 * kk + 2];
+                Q20 += Sc[6 + kk] * Gc[3 * kk + 0] - Gc[6 + kk] * Sc[3 * kk + 0];
+                Q01 += Sc[0 + kk] * Gc[3 * kk + 1] - Gc[0 + kk] * Sc[3 * kk + 1];
+            }
+            tw[3] += 2.f * Q12; tw[4] += 2.f * Q20; tw[5] += 2.f * Q01;
+            dO += gr[kGO];
+            // colour
+            if (D == 0) {
+                dk[0] += gr[kGR]; dk[1] += gr[kGG]; dk[2] += gr[kGBl];
+            } else {
+                float C[3];
+                cam_centre(T, C);
+                float ddx = m[0] - C[0], ddy = m[1] - C[1], ddz = m[2] - C[2];
+                float in = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+                float hx = ddx * in, hy = ddy * in, hz = ddz * in;
+                float Y[16];
+                sh_basis<D>(hx, hy, hz, Y);
+                float gcol[3] = {gr[kGR], gr[kGG], gr[kGBl]};
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    float c = k[ch];
+#pragma unroll
+                    for (int i = 1; i < NC; ++i) c += Y[i] * k[3 * i + ch];
+                    if (!(c > 0.f)) gcol[ch] = 0.f;  // clamped at zero
+                }
+                float w[16];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    dk[3 * i] += Y[i] * gcol[0];
+                    dk[3 * i + 1] += Y[i] * gcol[1];
+                    dk[3 * i + 2] += Y[i] * gcol[2];
+                    w[i] = gcol[0] * k[3 * i] + gcol[1] * k[3 * i + 1] + gcol[2] * k[3 * i + 2];
+                }
+                float3 gh = sh_weighted_grad<D>(hx, hy, hz, w);
+                float dd = gh.x * hx + gh.y * hy + gh.z * hz;
+                float dx_ = (gh.x - hx * dd) * in, dy_ = (gh.y - hy * dd) * in, dz_ = (gh.z - hz * dd) * in;
+                dmu[0] += dx_; dmu[1] += dy_; dmu[2] += dz_;
+                // the camera centre moves by -W^T rho: d rho += W ddir
+                tw[0] += T[0] * dx_ + T[1] * dy_ + T[2] * dz_;
+                tw[1] += T[4] * dx_ + T[5] * dy_ + T[6] * dz_;
+                tw[2] += T[8] * dx_ + T[9] * dy_ + T[10] * dz_;
+            }
+        }
+        // warp reduce the twist contributions of this view (fixed order)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float x = tw[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) s_tw[warp][v][i] = x;
+        }
+    }
+
+    if (ok) {
+        // Sig = M M^T with M = R diag(s): dM = 2 dSig M
+        float S[9];
+        sym_full(dSig, S);
+        float M[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M[3 * i + j] = A.R[3 * i + j] * A.s[j];
+        float dR[9], ds[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float dMij = 2.f * (S[3 * i] * M[j] + S[3 * i + 1] * M[3 + j] + S[3 * i + 2] * M[6 + j]);
+                ds[j] += dMij * A.R[3 * i + j];
+                dR[3 * i + j] = dMij * A.s[j];
+            }
+        float w = A.qn[0], x = A.qn[1], y = A.qn[2], z = A.qn[3];
+        float dq[4];
+        dq[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+        dq[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                       2.f * x * dR[8]);
+        dq[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                       2.f * y * dR[8]);
+        dq[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                       x * dR[6] + y * dR[7]);
+        float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+        float dqq[4] = {(dq[0] - w * dot) * A.qinv, (dq[1] - x * dot) * A.qinv, (dq[2] - y * dot) * A.qinv,
+                        (dq[3] - z * dot) * A.qinv};
+        float dls[3] = {ds[0] * A.s[0], ds[1] * A.s[1], ds[2] * A.s[2]};
+        float dol = dO * A.opacity * (1.f - A.opacity);
+        const bool acc = a.accumulate != 0;
+        if (a.d_means) {
+            float *o = a.d_means + 3 * g;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) o[i] = acc ? o[i] + dmu[i] : dmu[i];
+        }
+        if (a.d_log_scales) {
+            float *o = a.d_log_scales + 3 * g;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) o[i] = acc ? o[i] + dls[i] : dls[i];
+        }
+        if (a.d_quats) {
+            float4 *o = reinterpret_cast<float4 *>(a.d_quats) + g;
+            float4 val = make_float4(dqq[0], dqq[1], dqq[2], dqq[3]);
+            if (acc) {
+                float4 old = *o;
+                val.x += old.x; val.y += old.y; val.z += old.z; val.w += old.w;
+            }
+            *o = val;
+        }
+        if (a.d_opacity_logits) a.d_opacity_logits[g] = acc ? a.d_opacity_logits[g] + dol : dol;
+        if (a.d_colors) {
+            float *o = a.d_colors + g * NC * 3;
+#pragma unroll
+            for (int i = 0; i < NC * 3; ++i) o[i] = acc ? o[i] + dk[i] : dk[i];
+        }
+    } else if (live) {
+        // invalid quaternion: the Gaussian is never rendered, its gradient is zero
+        const bool acc = a.accumulate != 0;
+        if (!acc) {
+            if (a.d_means) for (int i = 0; i < 3; ++i) a.d_means[3 * g + i] = 0.f;
+            if (a.d_log_scales) for (int i = 0; i < 3; ++i) a.d_log_scales[3 * g + i] = 0.f;
+            if (a.d_quats) for (int i = 0; i < 4; ++i) a.d_quats[4 * g + i] = 0.f;
+            if (a.d_opacity_logits) a.d_opacity_logits[g] = 0.f;
+            if (a.d_colors) for (int i = 0; i < NC * 3; ++i) a.d_colors[g * NC * 3 + i] = 0.f;
+        }
+    }
+
+    __syncthreads();
+    // block partial of the twist, summed over warps in a fixed order
+    for (int i = threadIdx.x; i < vb.n_views * 6; i += blockDim.x) {
+        int v = i / 6, c = i % 6;
+        float s = 0.f;
+        for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += s_tw[wv][v][c];
+        a.twist_partial[((long long)blockIdx.x * vb.n_views + v) * 6 + c] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    int grid = (int)((a.n + 255) / 256);
+    switch (a.sh_degree) {
+    case 0: project_kernel<0><<<grid, 256, 0, s>>>(a, vb); break;
+    case 1: project_kernel<1><<<grid, 256, 0, s>>>(a, vb); break;
+    case 2: project_kernel<2><<<grid, 256, 0, s>>>(a, vb); break;
+    default: project_kernel<3><<<grid, 256, 0, s>>>(a, vb); break;
+    }
+    return cudaGetLastError();
+}
+
+int project_bwd_grid(long long n) { return (int)((n + 255) / 256); }
+
+cudaError_t launch_project_bwd(const ProjectBwdArgs &a, const ViewBatch &vb, int *grid_out, cudaStream_t s) {
+    int grid = project_bwd_grid(a.n);
+    if (grid_out) *grid_out = grid;
+    if (a.n == 0) return cudaSuccess;
+    switch (a.sh_degree) {
+    case 0: project_bwd_kernel<0><<<grid, 256, 0, s>>>(a, vb); break;
+    case 1: project_bwd_kernel<1><<<grid, 256, 0, s>>>(a, vb); break;
+    case 2: project_bwd_kernel<2><<<grid, 256, 0, s>>>(a, vb); break;
+    default: project_bwd_kernel<3><<<grid, 256, 0, s>>>(a, vb); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace s3gs

@@ -1,0 +1,164 @@
+// Fixed-order reductions: the per-view camera twist (Eq. 11), the
+// deterministic per-record sum of per-tile gradient partials, and the L1
+// mapping/tracking loss (Eq. 10, 15, 17) with its gradient.
+#include "s3gs_internal.cuh"
+
+namespace s3gs {
+namespace {
+
+// One block per view: sum of the per-block twist partials in a fixed order.
+__global__ void __launch_bounds__(256) twist_reduce_kernel(const TwistReduceArgs a) {
+    __shared__ float s[8][6];
+    const int v = blockIdx.x;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int p = threadIdx.x; p < a.n_parts; p += blockDim.x) {
+        const float *src = a.twist_partial + ((long long)p * a.n_views + v) * 6;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += src[c];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float x = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float x = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s[w][threadIdx.x];
+        float *dst = a.d_twist + v * 6 + threadIdx.x;
+        *dst = a.accumulate ? *dst + x : x;
+    }
+}
+
+// Deterministic mode: each visible record gathers its per-tile partials, tile
+// by tile in row-major order; its position inside each tile's list is found by
+// binary search of its unique (depth bits, index) key.
+__global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, const __grid_constant__ ViewBatch vb) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long total = (long long)vb.n_views * a.n;
+    if (r >= total) return;
+    int2 ext = a.ext[r];
+    if (ext.x <= 0) return;
+    int v = (int)(r / a.n);
+    unsigned g = (unsigned)(r - (long long)v * a.n);
+    const ViewInfo &vi = vb.v[v];
+    float4 ra = a.rec[r].a;
+    float z = a.rec[r].b.z;
+    float x0 = ceilf(__fsub_rn(ra.x, (float)ext.x)), x1 = floorf(__fadd_rn(ra.x, (float)ext.x));
+    float y0 = ceilf(__fsub_rn(ra.y, (float)ext.y)), y1 = floorf(__fadd_rn(ra.y, (float)ext.y));
+    int tx0 = (x0 > 0.f ? (int)x0 : 0) / vb.tile_w;
+    int tx1 = (x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1) / vb.tile_w;
+    int ty0 = (y0 > 0.f ? (int)y0 : 0) / vb.tile_h;
+    int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
+    const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | g;
+    float acc[kGrad2d];
+#pragma unroll
+    for (int q = 0; q < kGrad2d; ++q) acc[q] = 0.f;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            int t = vi.tile_base + ty * vi.tiles_x + tx;
+            unsigned lo = a.tile_start[t], hi = a.tile_start[t + 1];
+            while (lo < hi) {
+                unsigned mid = lo + ((hi - lo) >> 1);
+                if (a.keys[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            const float *src = a.det_partial + (long long)lo * kGrad2d;
+#pragma unroll
+            for (int q = 0; q < kGrad2d; ++q) acc[q] += src[q];
+        }
+    float *dst = a.grad2d + r * kGrad2d;
+#pragma unroll
+    for (int q = 0; q < kGrad2d; ++q) dst[q] = acc[q];
+}
+
+constexpr int kLossThreads = 256;
+
+__device__ __forceinline__ float sgn(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+__device__ __forceinline__ float l1_term(const float *x, const float *t, float *d, long long i, float c) {
+    float r = x[i] - t[i];
+    if (d) d[i] = c * sgn(r);
+    return c * fabsf(r);
+}
+
+// grid.y = view; every thread handles whole pixels (all channels of each term).
+__global__ void __launch_bounds__(kLossThreads) loss_kernel(const LossArgs a, const __grid_constant__ ViewBatch vb) {
+    __shared__ float s[kLossThreads / 32];
+    const int v = blockIdx.y;
+    const ViewInfo &vi = vb.v[v];
+    const long long HW = (long long)vi.w * vi.h;
+    const long long p1 = vi.pix_base, p3 = 3 * vi.pix_base;
+    const float P = (float)vb.total_pixels;
+    float acc = 0.f;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += (long long)gridDim.x * blockDim.x) {
+        const float m = a.mask ? a.mask[p1 + p] : 1.f;
+        const float cr = m * a.w_rgb / (3.f * P), cd = m * a.w_depth / P, cg = m * a.w_geo / (3.f * P);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const long long i = p3 + ch * HW + p;
+            if (a.t_rgb) acc += l1_term(a.rgb, a.t_rgb, a.d_rgb, i, cr);
+            else if (a.d_rgb) a.d_rgb[i] = 0.f;
+            if (a.t_pointmap) acc += l1_term(a.pointmap, a.t_pointmap, a.d_pointmap, i, cg);
+            else if (a.d_pointmap) a.d_pointmap[i] = 0.f;
+        }
+        if (a.t_depth) acc += l1_term(a.depth, a.t_depth, a.d_depth, p1 + p, cd);
+        else if (a.d_depth) a.d_depth[p1 + p] = 0.f;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float x = 0.f;
+        for (int w = 0; w < kLossThreads / 32; ++w) x += s[w];
+        a.partial[(long long)v * gridDim.x + blockIdx.x] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) loss_final_kernel(const float *partial, int n, float *loss) {
+    __shared__ float s[8];
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float x = 0.f;
+        for (int w = 0; w < 8; ++w) x += s[w];
+        *loss = x;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_twist_reduce(const TwistReduceArgs &a, cudaStream_t s) {
+    if (a.n_views <= 0) return cudaSuccess;
+    twist_reduce_kernel<<<a.n_views, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int loss_blocks_per_view() { return 64; }
+
+cudaError_t launch_loss(const LossArgs &a, const ViewBatch &vb, cudaStream_t s) {
+    dim3 grid(loss_blocks_per_view(), vb.n_views);
+    loss_kernel<<<grid, kLossThreads, 0, s>>>(a, vb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    loss_final_kernel<<<1, 256, 0, s>>>(a.partial, loss_blocks_per_view() * vb.n_views, a.loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_det_reduce(const DetReduceArgs &a, const ViewBatch &vb, cudaStream_t s) {
+    long long total = (long long)vb.n_views * a.n;
+    if (total == 0) return cudaSuccess;
+    det_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a, vb);
+    return cudaGetLastError();
+}
+
+}  // namespace s3gs

@@ -1,0 +1,234 @@
+// Internal declarations of the sm_103a Gaussian-splatting library.
+//
+// Pipeline of one forward (all views of a call in one pass per stage):
+//   project_kernel      EWA projection + colour of every (view, Gaussian) record
+//                       and per-tile duplicate counts              (Eq. 1, Sec. 3.1)
+//   scan_*              exclusive scan of the tile counts -> tile ranges, total K
+//   emit_kernel         bucket (depth, index) keys into their tiles
+//   tile_sort_kernel    per-tile sort of the keys by (depth, index)  (Eq. 3 order)
+//   blend_fwd_kernel    front-to-back compositing per tile          (Eq. 2-5)
+// and of one backward:
+//   blend_bwd_kernel    back-to-front per tile, warp-reduced gradients   (Eq. 11)
+//   det_reduce_kernel   (deterministic mode) fixed-order sum of per-tile partials
+//   project_bwd_kernel  chain to Gaussian parameters and per-view twist partials
+//   twist_reduce_kernel fixed-order sum of the twist partials
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/s3gs.h"
+
+namespace s3gs {
+
+// Rendering constants (the 3DGS rules the paper inherits; see s3gs.h).
+constexpr float kDilation = 0.3f;
+constexpr float kCutoffQ = 9.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr int kExtentMax = 1 << 24;  // clamp of the integer half-extent of a tile cover
+constexpr int kGrad2d = 10;          // per-record 2D gradient slots
+
+// 2D gradient slot order of a record.
+enum { kGU = 0, kGV, kGA, kGB, kGC, kGO, kGR, kGG, kGBl, kGZ };
+
+struct ViewInfo {
+    int w, h;
+    float fx, fy, cx, cy;
+    float T[12];   // world-to-camera, row-major 3x4
+    int tiles_x, tiles_y;
+    int tile_base;  // first global tile id of this view
+    int pad;
+    long long pix_base;  // first pixel of this view in the packed outputs
+};
+
+struct ViewBatch {
+    int n_views;
+    int tile_w, tile_h;
+    int total_tiles;
+    long long total_pixels;
+    ViewInfo v[S3GS_MAX_VIEWS];
+};
+
+// One projected (view, Gaussian) record: 48 bytes, read as three float4.
+struct __align__(16) Record {
+    float4 a;  // u, v, A, B  (conic = [[A, B], [B, C]])
+    float4 b;  // C, opacity, z, unused
+    float4 c;  // r, g, b, unused
+};
+
+struct DevCounters {
+    unsigned long long n_dup;     // total (Gaussian, tile) pairs K of the last forward
+    unsigned int overflow;        // 1 if K exceeded the key capacity
+    unsigned int work_fwd;        // persistent-grid work counters
+    unsigned int work_bwd;
+    unsigned int pad;
+    unsigned long long fwd_processed, fwd_blended, bwd_processed;
+};
+
+// Read a view's pose: the device override if given, else the camera's.
+__device__ __forceinline__ void load_pose(const ViewInfo &vi, const float *Tdev, int v, float T[12]) {
+    if (Tdev) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) T[k] = __ldg(Tdev + 12 * v + k);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) T[k] = vi.T[k];
+    }
+}
+
+__device__ __forceinline__ int view_of_tile(const ViewBatch &vb, int t) {
+    int v = 0;
+    for (int k = 1; k < vb.n_views; ++k)
+        if (t >= vb.v[k].tile_base) v = k;
+    return v;
+}
+
+// Per-pair quantities shared by the forward, the recompute replay and the
+// backward. Explicit round-to-nearest intrinsics keep the three bit-identical,
+// so that the backward takes exactly the forward's cutoff/skip/stop decisions.
+struct PairEval {
+    float dx, dy, q, G, alpha;
+    bool pass;     // inside the 3-sigma ellipse and alpha >= 1/255
+    bool clamped;  // alpha hit the 0.99 clamp
+};
+
+__device__ __forceinline__ PairEval eval_pair(float px, float py, float u, float v, float A, float B,
+                                              float C, float opacity) {
+    PairEval e;
+    e.dx = __fsub_rn(px, u);
+    e.dy = __fsub_rn(py, v);
+    // q = A dx^2 + 2 B dx dy + C dy^2 = dx (A dx + 2 B dy) + C dy^2
+    float t = __fmaf_rn(A, e.dx, __fmul_rn(__fmul_rn(2.0f, B), e.dy));
+    e.q = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(C, e.dy), e.dy));
+    e.G = __expf(__fmul_rn(-0.5f, e.q));
+    float a = __fmul_rn(opacity, e.G);
+    e.clamped = a >= kAlphaMax;
+    e.alpha = e.clamped ? kAlphaMax : a;
+    e.pass = (e.q <= kCutoffQ) && (e.alpha >= kAlphaMin);
+    return e;
+}
+
+__device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }
+
+// ---- launch wrappers (one per translation unit) ----
+struct ProjectArgs {
+    const float *means, *log_scales, *quats, *opacity_logits, *colors;
+    long long n;
+    int sh_degree;
+    float near_z;
+    const float *Tdev;
+    Record *rec;
+    int2 *ext;
+    unsigned *tile_count;
+};
+cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s);
+
+struct ScanArgs {
+    const unsigned *tile_count;
+    unsigned *tile_start;  // [T + 1]
+    unsigned *cursor;      // [T]
+    unsigned *partials;    // [ceil(T / 4096) + 1]
+    DevCounters *ctr;
+    long long n_tiles;
+    unsigned long long key_capacity;
+};
+cudaError_t launch_scan(const ScanArgs &a, cudaStream_t s);
+
+struct EmitArgs {
+    const Record *rec;
+    const int2 *ext;
+    long long n;
+    unsigned *cursor;
+    unsigned long long *keys;
+    unsigned long long key_capacity;
+    const DevCounters *ctr;
+};
+cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s);
+
+struct SortArgs {
+    const unsigned *tile_start;
+    unsigned long long *keys;
+    long long n_tiles;
+    const DevCounters *ctr;
+};
+cudaError_t launch_tile_sort(const SortArgs &a, cudaStream_t s);
+
+struct OrderArgs {
+    const unsigned *tile_start;
+    unsigned *order;       // [T] tiles, heaviest first (approximate, by log2 bucket)
+    unsigned *bucket_cnt;  // [33] scratch
+    long long n_tiles;
+};
+cudaError_t launch_tile_order(const OrderArgs &a, cudaStream_t s);
+
+struct BlendArgs {
+    const Record *rec;
+    const unsigned long long *keys;
+    const unsigned *tile_start;
+    const unsigned *order;  // may be NULL: natural tile order
+    long long n;
+    float bg[3];
+    // forward outputs
+    float *rgb, *depth, *pointmap, *alpha;
+    float *T_final;     // per-pixel state (NULL in recompute mode)
+    unsigned *n_last;   // per-pixel state (NULL in recompute mode)
+    // backward inputs / outputs
+    const float *d_rgb, *d_depth, *d_pointmap, *d_alpha;
+    float *grad2d;      // [records][10] atomic accumulation
+    float *det_partial; // [K][10] deterministic mode, else NULL
+    DevCounters *ctr;
+    int persistent;     // 0: one CTA per tile
+    int batch;
+    int counting;
+};
+cudaError_t launch_blend_fwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
+cudaError_t launch_blend_bwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
+
+struct DetReduceArgs {
+    const Record *rec;
+    const int2 *ext;
+    const unsigned long long *keys;
+    const unsigned *tile_start;
+    const float *det_partial;
+    float *grad2d;
+    long long n;
+};
+cudaError_t launch_det_reduce(const DetReduceArgs &a, const ViewBatch &vb, cudaStream_t s);
+
+struct ProjectBwdArgs {
+    const float *means, *log_scales, *quats, *opacity_logits, *colors;
+    long long n;
+    int sh_degree;
+    const float *Tdev;
+    const int2 *ext;
+    float *grad2d;  // read, then cleared to zero for the next backward
+    float *d_means, *d_log_scales, *d_quats, *d_opacity_logits, *d_colors;
+    int accumulate;
+    float *twist_partial;  // [gridDim.x][n_views][6]
+};
+cudaError_t launch_project_bwd(const ProjectBwdArgs &a, const ViewBatch &vb, int *grid_out,
+                               cudaStream_t s);
+int project_bwd_grid(long long n);
+
+struct TwistReduceArgs {
+    const float *twist_partial;
+    int n_parts;
+    int n_views;
+    float *d_twist;
+    int accumulate;
+};
+cudaError_t launch_twist_reduce(const TwistReduceArgs &a, cudaStream_t s);
+
+struct LossArgs {
+    const float *rgb, *depth, *pointmap, *t_rgb, *t_depth, *t_pointmap, *mask;
+    float w_rgb, w_depth, w_geo;
+    float *d_rgb, *d_depth, *d_pointmap;
+    float *partial;  // [loss_blocks_per_view() * n_views]
+    float *loss;
+};
+int loss_blocks_per_view();
+cudaError_t launch_loss(const LossArgs &a, const ViewBatch &vb, cudaStream_t s);
+
+}  // namespace s3gs

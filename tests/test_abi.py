@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every declared entry point.
+
+No compute call is made here (no GPU is needed).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "s3gs.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(s3gs_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+    from paper_2507_03737_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("s3gs_create", "s3gs_destroy", "s3gs_render_fwd", "s3gs_render_bwd", "s3gs_reserve",
+                 "s3gs_state_create", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    lib.s3gs_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.s3gs_version()
+    from paper_2507_03737_gb300 import binding as B
+    o = B.s3gs_options_default()
+    assert (o.tile_w, o.tile_h, o.auto_grow) == (16, 16, 1)
+    assert abs(o.near_z - 0.2) < 1e-7
+    # null arguments are rejected without touching the GPU
+    assert lib.s3gs_create(0, None) == B.S3GS_E_INVALID
+
+
+def test_binding_struct_layout_matches_header():
+    from paper_2507_03737_gb300 import binding as B
+    assert ctypes.sizeof(B.Camera) == 4 * (2 + 4 + 12)
+    assert ctypes.sizeof(B.Options) == 4 * (7 + 1 + 3)
+    assert B.Gaussians.means.offset == 16
+
+
+def test_no_cpu_fallback_in_product_package():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2507_03737_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "s3gs_oracle" not in src, f

@@ -1,0 +1,344 @@
+"""GPU path against the FP64 oracle through the C ABI (config 1 and variations).
+
+Forward outputs element by element, binning bit-exactly against the integer
+referee, gradients per tensor, plus the equivalences the design promises
+(batched = per view, persistent = flat grid, recompute = stored state,
+deterministic runs bitwise equal).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2507_03737_gb300 import scenes
+from tests.gpu_helpers import (compare_forward, compare_grads, expand3, pixel_mask, rel_l2,
+                               upstream)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2507_03737_gb300.autograd import Renderer
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def _opts(**kw):
+    from paper_2507_03737_gb300 import binding as B
+    return B.s3gs_options_default(**kw)
+
+
+def test_projection_matches_oracle(R):
+    from paper_2507_03737_gb300 import binding as B
+    sc = scenes.config_scene(1)
+    R.render_np(sc)
+    rec = B.s3gs_debug_records(R.ctx, R.state, sc.n)
+    ref = O.project(sc, sc.cameras[0])
+    vis = rec["extent"][:, 0] > 0
+    assert vis.sum() > 0.5 * sc.n
+    assert np.all(ref["valid"][vis] > 0)
+    conic_norm = np.maximum(np.abs(ref["A"]), np.abs(ref["C"]))[vis]
+    for k, col in (("u", rec["xy"][:, 0]), ("v", rec["xy"][:, 1]), ("A", rec["conic_opacity"][:, 0]),
+                   ("B", rec["conic_opacity"][:, 1]), ("C", rec["conic_opacity"][:, 2]),
+                   ("opacity", rec["conic_opacity"][:, 3]), ("depth", rec["rgb_depth"][:, 3]),
+                   ("r", rec["rgb_depth"][:, 0])):
+        a, b = col[vis].astype(np.float64), ref[k][vis]
+        # conic entries relative to the conic's norm; pixel coordinates relative to |u| + 1 px
+        scale = conic_norm if k in ("A", "B", "C") else np.abs(b) + (1.0 if k in ("u", "v") else 0.0)
+        assert np.max(np.abs(a - b) / scale) < 2e-5, k
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (16, 8), (8, 8), (32, 8)])
+def test_binning_bit_exact(R, tile):
+    from paper_2507_03737_gb300 import binding as B
+    sc = scenes.tiny_scene(5, n=300, width=77, height=45, n_views=3, scale=0.2)
+    sc.cameras[1] = dict(sc.cameras[1], width=33, height=70)
+    sc.cameras[2] = dict(sc.cameras[2], width=16, height=16)
+    opt = _opts(tile_w=tile[0], tile_h=tile[1])
+    R.render_np(sc, options=opt)
+    rec = B.s3gs_debug_records(R.ctx, R.state, sc.n * 3)
+    keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
+    wh = [(c["width"], c["height"]) for c in sc.cameras]
+    rk, rv, rr = O.bin_referee(wh, tile[0], tile[1], rec["xy"][:, 0], rec["xy"][:, 1], rec["extent"][:, 0],
+                               rec["extent"][:, 1], rec["rgb_depth"][:, 3])
+    assert keys.size == rk.size > 0
+    assert np.array_equal(keys, rk)
+    assert np.array_equal(vals, rv)
+    assert np.array_equal(ranges, rr)
+
+
+def test_forward_config1(R):
+    sc = scenes.config_scene(1)
+    gpu = R.render_np(sc)
+    ref = O.render_fwd(sc)
+    res = compare_forward(gpu, ref, sc.cameras)
+    assert res["excluded"] < 100
+
+
+def test_backward_config1(R):
+    sc = scenes.config_scene(1)
+    ref_f = O.render_fwd(sc)
+    mask = pixel_mask(ref_f)
+    ups = upstream(sc.cameras, 7, mask)
+    R.render_np(sc)
+    g = R.backward_np(ups, 1)
+    gref = O.render_bwd(sc, **ups)
+    compare_grads(g, gref)
+
+
+@pytest.mark.parametrize("deg", [1, 3])
+def test_sh_forward_backward(R, deg):
+    sc = scenes.tiny_scene(61 + deg, n=40, width=40, height=30, sh_degree=deg, n_views=2, scale=0.2)
+    ref_f = O.render_fwd(sc)
+    gpu = R.render_np(sc)
+    compare_forward(gpu, ref_f, sc.cameras)
+    mask = pixel_mask(ref_f)
+    ups = upstream(sc.cameras, 3, mask)
+    g = R.backward_np(ups, 2)
+    compare_grads(g, O.render_bwd(sc, **ups))
+
+
+def test_multiview_uneven_ragged(R):
+    """Uneven, non-multiple-of-tile resolutions and shifted principal points."""
+    sc = scenes.config_scene(1, n_override=3000)
+    base = sc.cameras[0]
+    rng = np.random.default_rng(2)
+    cams = [base]
+    for (w, h) in [(37, 53), (161, 7), (1, 1), (64, 48)]:
+        T = scenes.look_at_pose(rng.uniform(-0.5, 0.5, 3), yaw=rng.uniform(-0.1, 0.1))
+        cams.append(scenes.camera(w, h, 150.0, 150.0, w / 2 + rng.uniform(-9, 9), h / 2 + rng.uniform(-9, 9), T))
+    sc.cameras = cams
+    ref_f = O.render_fwd(sc)
+    for tile in [(16, 16), (8, 8), (32, 8)]:
+        gpu = R.render_np(sc, options=_opts(tile_w=tile[0], tile_h=tile[1]))
+        compare_forward(gpu, ref_f, cams)
+    mask = pixel_mask(ref_f)
+    ups = upstream(cams, 11, mask)
+    g = R.backward_np(ups, len(cams))
+    compare_grads(g, O.render_bwd(sc, **ups))
+
+
+def test_crop_equals_window(R):
+    """Shifted principal point: a crop equals the window of the full render (GPU vs GPU, bitwise
+    up to the projection's rounding of u, v)."""
+    sc = scenes.config_scene(1)
+    full = R.render_np(sc)
+    cam = sc.cameras[0]
+    x0, y0, w, h = 37, 21, 64, 48
+    crop = dict(cam, width=w, height=h, cx=cam["cx"] - x0, cy=cam["cy"] - y0)
+    out = R.render_np(sc, cameras=[crop])
+    ref = O.render_fwd(sc, cameras=[crop])
+    compare_forward(out, ref, [crop])
+    a = full["rgb"].reshape(3, 120, 160)[:, y0:y0 + h, x0:x0 + w]
+    assert np.abs(out["rgb"].reshape(3, h, w) - a).max() < 1e-4
+
+
+def test_batched_equals_per_view(R):
+    import torch
+    sc = scenes.tiny_scene(8, n=400, width=64, height=40, n_views=4, scale=0.15)
+    full = R.render_np(sc)
+    ups = upstream(sc.cameras, 4)
+    g_all = R.backward_np(ups, 4)
+    off = 0
+    acc = None
+    for v, cam in enumerate(sc.cameras):
+        hw = cam["width"] * cam["height"]
+        one = R.render_np(sc, cameras=[cam])
+        for k, ch in (("rgb", 3), ("depth", 1), ("pointmap", 3), ("alpha", 1)):
+            np.testing.assert_array_equal(one[k], full[k][ch * off: ch * (off + hw)])
+        sub = {k: (u[3 * off: 3 * (off + hw)] if u.size == 3 * sum(c["width"] * c["height"] for c in sc.cameras)
+                   else u[off: off + hw]) for k, u in ups.items()}
+        g = R.backward_np(sub, 1)
+        np.testing.assert_allclose(g["twist"][0], g_all["twist"][v], rtol=1e-4, atol=1e-4)
+        acc = g if acc is None else {k: acc[k] + g[k] for k in acc if k != "twist"}
+        off += hw
+    for k in ("means", "log_scales", "quats", "opacity_logits", "colors"):
+        assert rel_l2(g_all[k], acc[k]) < 1e-5, k
+
+
+def test_persistent_and_recompute_and_det(R):
+    sc = scenes.tiny_scene(9, n=600, width=80, height=60, n_views=2, scale=0.15)
+    ups = upstream(sc.cameras, 5)
+    base = R.render_np(sc)
+    g0 = R.backward_np(ups, 2)
+    outs = {}
+    for name, kw in (("persistent", dict(blocks_per_sm=2)), ("recompute", dict(recompute=1)),
+                     ("det", dict(deterministic=1)), ("det_recompute", dict(deterministic=1, recompute=1)),
+                     ("det_persistent", dict(deterministic=1, blocks_per_sm=3, batch=64))):
+        out = R.render_np(sc, options=_opts(**kw))
+        for k in base:
+            np.testing.assert_array_equal(out[k], base[k], err_msg=f"{name} {k}")
+        outs[name] = R.backward_np(ups, 2)
+        for k in g0:
+            assert rel_l2(outs[name][k], g0[k]) < 1e-5, (name, k)
+    for k in g0:  # deterministic mode is bitwise reproducible, whatever the schedule
+        np.testing.assert_array_equal(outs["det"][k], outs["det_recompute"][k])
+        np.testing.assert_array_equal(outs["det"][k], outs["det_persistent"][k])
+    R.render_np(sc, options=_opts(deterministic=1))
+    again = R.backward_np(ups, 2)
+    for k in g0:
+        np.testing.assert_array_equal(again[k], outs["det"][k])
+
+
+def test_batch_size_and_tile_do_not_change_forward(R):
+    sc = scenes.config_scene(1)
+    base = R.render_np(sc)
+    for kw in (dict(batch=32), dict(batch=1024), dict(tile_w=8, tile_h=8, batch=17), dict(tile_w=32, tile_h=8)):
+        out = R.render_np(sc, options=_opts(**kw))
+        for k in base:
+            np.testing.assert_array_equal(out[k], base[k], err_msg=str(kw))
+
+
+def test_background_colour(R):
+    sc = scenes.tiny_scene(10, n=30, width=30, height=20, scale=0.2)
+    bg = (0.2, 0.5, 0.9)
+    gpu = R.render_np(sc, options=_opts(bg=bg))
+    ref = O.render_fwd(sc, bg=bg)
+    compare_forward(gpu, ref, sc.cameras)
+    mask = pixel_mask(ref)
+    ups = upstream(sc.cameras, 2, mask)
+    compare_grads(R.backward_np(ups, 1), O.render_bwd(sc, bg=bg, **ups))
+
+
+def test_heavy_tile_sort_path(R):
+    """Tiles with more than 4096 duplicates take the global-memory sort path."""
+    from paper_2507_03737_gb300 import binding as B
+    rng = np.random.default_rng(3)
+    n = 9000
+    means = np.stack([rng.uniform(-0.05, 0.05, n), rng.uniform(-0.05, 0.05, n), rng.uniform(2, 6, n)], 1)
+    sc = scenes.random_gaussians(rng, means, 0, np.log(0.01), 0.3)
+    sc.opacity_logits[:] = -4.0  # keep pixels from saturating so every duplicate is reached
+    sc.cameras = [scenes.camera(32, 32, 40.0, 40.0, 15.5, 15.5)]
+    gpu = R.render_np(sc)
+    keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
+    assert np.diff(ranges).max() > 4096
+    rec = B.s3gs_debug_records(R.ctx, R.state, n)
+    rk, rv, rr = O.bin_referee([(32, 32)], 16, 16, rec["xy"][:, 0], rec["xy"][:, 1], rec["extent"][:, 0],
+                               rec["extent"][:, 1], rec["rgb_depth"][:, 3])
+    assert np.array_equal(keys, rk) and np.array_equal(vals, rv) and np.array_equal(ranges, rr)
+    # a deliberately dense stack: more pixels sit near a threshold than in the workloads
+    compare_forward(gpu, O.render_fwd(sc), sc.cameras, max_excluded=0.05)
+
+
+def test_edge_cases(R):
+    from paper_2507_03737_gb300 import binding as B
+    cam = scenes.camera(20, 10, 20.0, 20.0, 9.5, 4.5)
+    # empty scene: background only
+    empty = scenes.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32),
+                         np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0, [cam])
+    import torch
+    p = {k: torch.zeros((1,) + v.shape[1:], device="cuda")[:0] for k, v in
+         dict(means=empty.means, log_scales=empty.log_scales, quats=torch.zeros(0, 4),
+              opacity_logits=torch.zeros(0), colors=torch.zeros(0, 1, 3)).items()}
+    p["sh_degree"] = 0
+    out = R.forward(p, [cam], options=_opts(bg=(0.1, 0.2, 0.3)))
+    rgb = out["rgb"].cpu().numpy().reshape(3, -1)
+    assert np.allclose(rgb[0], 0.1) and np.allclose(rgb[2], 0.3) and float(out["alpha"].abs().max()) == 0.0
+    g = R.backward(p, 1, {"rgb": torch.ones(600, device="cuda")})
+    assert float(g["twist"].abs().max()) == 0.0
+    # everything behind the camera or beyond the image
+    sc = scenes.tiny_scene(12, n=10, width=20, height=10)
+    sc.means[:5, 2] = -3.0
+    sc.means[5:, 0] = 50.0
+    out = R.render_np(sc)
+    assert np.abs(out["alpha"]).max() == 0.0
+    # one Gaussian filling the view
+    one = scenes.tiny_scene(13, n=1, width=24, height=20, scale=2.0)
+    compare_forward(R.render_np(one), O.render_fwd(one), one.cameras)
+
+
+def test_errors_are_reported(R):
+    import torch
+    from paper_2507_03737_gb300 import binding as B
+    sc = scenes.tiny_scene(14, n=50, width=40, height=30)
+    p = R.upload(sc)
+    st = R.acquire()
+    with pytest.raises(B.S3GSError) as e:
+        R.backward(p, 1, {}, state=st)
+    assert e.value.status == B.S3GS_E_STATE
+    for cams, kw, status in (
+            ([], {}, B.S3GS_E_INVALID),
+            ([sc.cameras[0]] * 33, {}, B.S3GS_E_INVALID),
+            (sc.cameras, dict(tile_w=12, tile_h=12), B.S3GS_E_INVALID),
+            ([dict(sc.cameras[0], fx=float("nan"))], {}, B.S3GS_E_INVALID),
+            ([dict(sc.cameras[0], width=0)], {}, B.S3GS_E_INVALID)):
+        with pytest.raises(B.S3GSError) as e:
+            R.forward(p, cams if cams else [sc.cameras[0]], options=_opts(**kw), state=st) if cams else \
+                B.s3gs_render_fwd(R.ctx, st, B.make_gaussians(p["means"], p["log_scales"], p["quats"],
+                                                              p["opacity_logits"], p["colors"], 0),
+                                  B.make_cameras(sc.cameras), 0, None, _opts(), None, None, None, None)
+        assert e.value.status == status
+    bad = dict(p, sh_degree=4)
+    with pytest.raises(B.S3GSError):
+        R.forward(bad, sc.cameras, state=st)
+    # capacity: a tiny reserved duplicate buffer without auto-grow
+    st2 = B.s3gs_state_create(R.ctx)
+    B.s3gs_reserve(R.ctx, st2, sc.n, 1, 40 * 30, 12, 4)
+    R.forward(p, sc.cameras, options=_opts(auto_grow=0), state=st2)
+    status, K, cap = B.s3gs_state_check(R.ctx, st2, raise_on_error=False)
+    assert status == B.S3GS_E_CAPACITY and K > cap == 4
+    # the same state recovers once auto-grow is allowed again
+    R.forward(p, sc.cameras, options=_opts(auto_grow=1), state=st2)
+    status, K2, cap2 = B.s3gs_state_check(R.ctx, st2, raise_on_error=False)
+    assert status == B.S3GS_OK and cap2 >= K2 == K
+    B.s3gs_state_destroy(st2)
+    R.release(st)
+    torch.cuda.synchronize()
+
+
+def test_mapping_loss_kernel(R):
+    import torch
+    from paper_2507_03737_gb300 import binding as B
+    rng = np.random.default_rng(0)
+    cams = [scenes.camera(33, 17, 30, 30, 16, 8), scenes.camera(20, 40, 30, 30, 10, 20)]
+    P = 33 * 17 + 20 * 40
+    t = lambda a: torch.as_tensor(a.astype(np.float32), device="cuda")
+    x = {k: rng.standard_normal(n) for k, n in (("rgb", 3 * P), ("depth", P), ("pm", 3 * P))}
+    y = {k: rng.standard_normal(v.size) for k, v in x.items()}
+    mask = (rng.uniform(size=P) > 0.3).astype(np.float64)
+    d = {k: torch.empty(v.size, device="cuda") for k, v in x.items()}
+    loss = torch.zeros(1, device="cuda")
+    w = (0.98, 0.5, 0.02)
+    B.s3gs_mapping_loss(R.ctx, B.make_cameras(cams), 2, t(x["rgb"]), t(x["depth"]), t(x["pm"]), t(y["rgb"]),
+                        t(y["depth"]), t(y["pm"]), t(mask), *w, d["rgb"], d["depth"], d["pm"], loss)
+    torch.cuda.synchronize()
+    m3 = expand3(mask, cams)
+    xr = {k: x[k].astype(np.float32).astype(np.float64) for k in x}
+    yr = {k: y[k].astype(np.float32).astype(np.float64) for k in y}
+    ref = (w[0] * np.sum(m3 * np.abs(xr["rgb"] - yr["rgb"])) / (3 * P) +
+           w[1] * np.sum(mask * np.abs(xr["depth"] - yr["depth"])) / P +
+           w[2] * np.sum(m3 * np.abs(xr["pm"] - yr["pm"])) / (3 * P))
+    assert abs(float(loss.item()) - ref) < 1e-5 * abs(ref)
+    np.testing.assert_allclose(d["rgb"].cpu().numpy(), w[0] * m3 * np.sign(xr["rgb"] - yr["rgb"]) / (3 * P),
+                               rtol=1e-5, atol=1e-12)
+    np.testing.assert_allclose(d["depth"].cpu().numpy(), w[1] * mask * np.sign(xr["depth"] - yr["depth"]) / P,
+                               rtol=1e-5, atol=1e-12)
+
+
+def test_autograd_function_and_pose_gradient(R):
+    """torch.autograd drives the CUDA backward; the twist gradient decreases a tracking loss."""
+    import torch
+    from paper_2507_03737_gb300.autograd import apply_twist, render
+    sc = scenes.tiny_scene(15, n=200, width=64, height=48, scale=0.15, max_opacity=0.9)
+    p = R.upload(sc)
+    cam = sc.cameras[0]
+    target = [t.detach() for t in render(R, p, [cam])]
+    off = dict(cam, T_cw=apply_twist(cam["T_cw"], np.array([0.02, -0.01, 0.0, 0.0, 0.01, -0.01])))
+    losses = []
+    for it in range(12):
+        tw = torch.zeros(1, 6, device="cuda", requires_grad=True)
+        rgb, depth, pm, alpha = render(R, p, [off], twist=tw)
+        loss = (rgb - target[0]).abs().mean()
+        loss.backward()
+        losses.append(float(loss))
+        g = tw.grad.detach().cpu().numpy()[0].astype(np.float64)
+        off = dict(off, T_cw=apply_twist(off["T_cw"], -2e-3 * g / max(np.linalg.norm(g), 1e-12)))
+    assert losses[-1] < losses[0]
+    # parameters receive gradients through the same Function
+    q = {k: (v.clone().requires_grad_(True) if k != "sh_degree" else v) for k, v in p.items()}
+    rgb, depth, pm, alpha = render(R, q, [cam])
+    (rgb.sum() + depth.sum()).backward()
+    assert float(q["means"].grad.abs().sum()) > 0 and float(q["colors"].grad.abs().sum()) > 0
