@@ -184,6 +184,29 @@ s3gs_status s3gs_mapping_loss(s3gs_ctx *ctx, const s3gs_camera *cams, int32_t n_
                               float *d_rgb, float *d_depth, float *d_pointmap, float *loss_device,
                               void *stream);
 
+/* Allocation-free variant of s3gs_mapping_loss (the paper has no counterpart:
+ * this is a deployment convenience). Same arguments, layout and result, but no
+ * context and no allocation: it calls no cudaMalloc/cudaFree and no allocating
+ * library routine. It is for callers that cannot allocate device memory --
+ * code running inside a global-mode CUDA stream capture, hosts whose device
+ * memory belongs to a pooling allocator or a fixed budget, and latency-bound
+ * loops that must avoid the implicit synchronisation of cudaMalloc/cudaFree.
+ * Its partial sums live in a fixed 8 KB static device array (64 per view, so
+ * n_views <= S3GS_MAX_VIEWS); larger requests return S3GS_E_INVALID. The first
+ * call on each device looks up that array's address (cudaGetSymbolAddress),
+ * so make one call per device before any stream capture. All calls share the
+ * array: calls that overlap on the GPU (e.g. on two concurrent streams) race
+ * and give wrong results; each call rewrites every partial it reads, so
+ * nothing needs clearing between calls. err (optional, err_len bytes) receives
+ * a message on failure; the status is INVALID for bad arguments or sizes and
+ * CUDA for runtime failures. */
+s3gs_status s3gs_mapping_loss_noalloc(const s3gs_camera *cams, int32_t n_views, const float *rgb,
+                                      const float *depth, const float *pointmap, const float *t_rgb,
+                                      const float *t_depth, const float *t_pointmap, const float *mask,
+                                      float w_rgb, float w_depth, float w_geo, float *d_rgb,
+                                      float *d_depth, float *d_pointmap, float *loss_device,
+                                      void *stream, char *err, size_t err_len);
+
 /* Diagnostics (synchronous; HOST output arrays, any may be NULL).
  * s3gs_debug_records: per record r = v * n + g of the last forward:
  *   xy [r][2], conic_opacity [r][4] (A, B, C, opacity), rgb_depth [r][4]

@@ -21,7 +21,7 @@ __all__ = [
     "s3gs_state_create", "s3gs_state_destroy", "s3gs_reserve", "s3gs_render_fwd",
     "s3gs_render_bwd", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_debug_records",
     "s3gs_debug_binning", "s3gs_set_counting", "s3gs_read_counters", "s3gs_version",
-    "s3gs_set_timing", "s3gs_read_timing", "STAGES",
+    "s3gs_set_timing", "s3gs_read_timing", "STAGES", "s3gs_mapping_loss_noalloc",
     "make_cameras", "make_gaussians", "check",
 ]
 
@@ -93,6 +93,9 @@ def _load():
         "s3gs_set_counting": (ctypes.c_int, [_P, ctypes.c_int32]),
         "s3gs_read_counters": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64),
                                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "s3gs_mapping_loss_noalloc": (ctypes.c_int, [ctypes.POINTER(Camera), ctypes.c_int32, _P, _P, _P, _P, _P,
+                                                     _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                                     _P, _P, _P, _P, _P, ctypes.c_char_p, ctypes.c_size_t]),
         "s3gs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
         "s3gs_read_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
         "s3gs_version": (ctypes.c_char_p, []),
@@ -233,6 +236,18 @@ def s3gs_mapping_loss(ctx, cams, n_views, rgb, depth, pointmap, t_rgb, t_depth, 
                                        float(w_rgb), float(w_depth), float(w_geo), _ptr(d_rgb),
                                        _ptr(d_depth), _ptr(d_pointmap), _ptr(loss_device),
                                        _stream(stream)))
+
+
+def s3gs_mapping_loss_noalloc(cams, n_views, rgb, depth, pointmap, t_rgb, t_depth, t_pointmap, mask,
+                              w_rgb, w_depth, w_geo, d_rgb, d_depth, d_pointmap, loss_device, stream=None):
+    """Allocation-free mapping loss (no context); raises S3GSError with the library's message."""
+    buf = ctypes.create_string_buffer(256)
+    st = lib().s3gs_mapping_loss_noalloc(cams, int(n_views), _ptr(rgb), _ptr(depth), _ptr(pointmap), _ptr(t_rgb),
+                                         _ptr(t_depth), _ptr(t_pointmap), _ptr(mask), float(w_rgb), float(w_depth),
+                                         float(w_geo), _ptr(d_rgb), _ptr(d_depth), _ptr(d_pointmap),
+                                         _ptr(loss_device), _stream(stream), buf, len(buf))
+    if st != S3GS_OK:
+        raise S3GSError(st, buf.value.decode())
 
 
 def s3gs_debug_records(ctx, state, n_records):
