@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--ppt", type=int, default=0, help="pixels per blend thread (0 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--deterministic", type=int, default=0)
     ap.add_argument("--recompute", type=int, default=0)
@@ -174,7 +175,8 @@ def workload_config(sc, args, extra=None):
                        f"SH degree {sc.sh_degree}, batched mapping-window fwd+loss+bwd",
            "n_gaussians": sc.n, "views": len(cams), "resolutions": res, "sh_degree": sc.sh_degree,
            "loss": f"L1 rgb {W_RGB} + depth {W_DEPTH} + pointmap {W_GEO} (Eq. 17)",
-           "tile": args.tile, "batch": args.batch or "tile pixels", "blocks_per_sm": args.blocks_per_sm,
+           "tile": args.tile, "batch": args.batch or 256, "pixels_per_thread": args.ppt or 2,
+           "blocks_per_sm": args.blocks_per_sm,
            "deterministic": args.deterministic, "recompute": args.recompute,
            "l2": "flushed between timed steps (256 MB write outside the step events)"}
     if extra:
@@ -224,8 +226,12 @@ class Workload:
         self.cams = sc.cameras
         self.V = len(self.cams)
         tw, th = tile_shape(args.tile)
-        self.opt = B.s3gs_options_default(tile_w=tw, tile_h=th, batch=args.batch, blocks_per_sm=args.blocks_per_sm,
+        self.opt = B.s3gs_options_default(tile_w=tw, tile_h=th, blocks_per_sm=args.blocks_per_sm,
                                           deterministic=args.deterministic, recompute=args.recompute)
+        if args.batch:
+            self.opt.batch = args.batch
+        if args.ppt:
+            self.opt.pixels_per_thread = args.ppt
         self.R = Renderer(device.index or 0, self.opt)
         self.p = self.R.upload(sc)
         P = sum(c["width"] * c["height"] for c in self.cams)

@@ -94,7 +94,8 @@ typedef struct {
  * order of atomically accumulated gradients (and nothing in deterministic mode). */
 typedef struct {
     int32_t tile_w, tile_h;  /* tile shape: 16x16 (default), 16x8, 8x8 or 32x8 */
-    int32_t batch;           /* Gaussians staged per shared-memory batch: 0 = tile_w*tile_h */
+    int32_t pixels_per_thread; /* pixels each blend thread owns: 1, 2 or 4 (0 = 2) */
+    int32_t batch;           /* Gaussians staged per shared-memory batch: 0 = 256 */
     int32_t blocks_per_sm;   /* blend kernels: 0 = one CTA per tile; k > 0 = persistent grid of
                                 k CTAs per SM pulling tiles (heaviest first) from a work counter */
     int32_t deterministic;   /* 1: gradients are bitwise reproducible run to run */
@@ -105,8 +106,9 @@ typedef struct {
     float bg[3];             /* background colour composited with the final transmittance */
 } s3gs_options;
 
-/* Fill *opt with the defaults (16x16 tiles, one CTA per tile, atomic gradients,
- * stored blend state, auto_grow = 1, near_z = 0.2, black background). */
+/* Fill *opt with the defaults (16x16 tiles, 2 pixels per thread, batches of 256,
+ * one CTA per tile, atomic gradients, stored blend state, auto_grow = 1,
+ * near_z = 0.2, black background). */
 void s3gs_options_default(s3gs_options *opt);
 
 /* Create a context on CUDA device `device`. *out receives the handle. */

@@ -165,7 +165,8 @@ bool valid_tile(int tw, int th) {
 void fill_options(const s3gs_options *in, s3gs_options &o) {
     if (in) o = *in; else s3gs_options_default(&o);
     if (o.tile_w == 0 && o.tile_h == 0) { o.tile_w = 16; o.tile_h = 16; }
-    if (o.batch <= 0) o.batch = o.tile_w * o.tile_h;
+    if (o.pixels_per_thread == 0) o.pixels_per_thread = 2;
+    if (o.batch <= 0) o.batch = 256;
     if (o.near_z == 0.f) o.near_z = 0.2f;
 }
 
@@ -230,7 +231,8 @@ void s3gs_options_default(s3gs_options *opt) {
     memset(opt, 0, sizeof(*opt));
     opt->tile_w = 16;
     opt->tile_h = 16;
-    opt->batch = 0;
+    opt->pixels_per_thread = 2;
+    opt->batch = 256;
     opt->blocks_per_sm = 0;
     opt->deterministic = 0;
     opt->recompute = 0;
@@ -370,6 +372,10 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     if (!valid_tile(opt.tile_w, opt.tile_h))
         return fail(ctx, S3GS_E_INVALID, "render_fwd: tile shape must be 16x16, 16x8, 8x8 or 32x8");
     if (opt.batch > 1024) return fail(ctx, S3GS_E_INVALID, "render_fwd: batch must be <= 1024");
+    if (opt.pixels_per_thread != 1 && opt.pixels_per_thread != 2 && opt.pixels_per_thread != 4)
+        return fail(ctx, S3GS_E_INVALID, "render_fwd: pixels_per_thread must be 1, 2 or 4");
+    if ((opt.tile_w * opt.tile_h / opt.pixels_per_thread) % 32 != 0)
+        return fail(ctx, S3GS_E_INVALID, "render_fwd: tile_w * tile_h / pixels_per_thread must be a multiple of 32");
     if (opt.blocks_per_sm < 0 || opt.blocks_per_sm > 64)
         return fail(ctx, S3GS_E_INVALID, "render_fwd: blocks_per_sm must be in 0..64");
     if (!(opt.near_z > 0.f) || !std::isfinite(opt.near_z))
@@ -462,6 +468,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     ba.ctr = st->ctr;
     ba.persistent = persistent;
     ba.batch = opt.batch;
+    ba.ppt = opt.pixels_per_thread;
     ba.counting = ctx->counting;
     long long grid = persistent ? std::min<long long>(T, (long long)ctx->num_sms * opt.blocks_per_sm) : T;
     {
@@ -514,6 +521,7 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
     ba.ctr = st->ctr;
     ba.persistent = persistent;
     ba.batch = st->opt.batch;
+    ba.ppt = st->opt.pixels_per_thread;
     ba.counting = ctx->counting;
     const long long T = vb.total_tiles;
     long long grid = persistent ? std::min<long long>(T, (long long)ctx->num_sms * st->opt.blocks_per_sm) : T;

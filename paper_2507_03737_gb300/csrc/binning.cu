@@ -114,31 +114,79 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const ScanArgs a) {
     }
 }
 
+// One warp expands the (record, tile) pairs of its 32 records: an inclusive
+// warp scan of the records' tile counts numbers the pairs, and each round every
+// lane takes one pair (found by a 5-step search of the scan), so all lanes stay
+// busy whatever the mix of visible, culled, small and large records. Four rounds
+// of cursor atomics are issued before their results are consumed.
 __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __grid_constant__ ViewBatch vb) {
+    __shared__ unsigned s_incl[8][32], s_excl[8][32], s_origin[8][32], s_ntx[8][32], s_tx[8][32];
+    __shared__ unsigned long long s_key[8][32];
     if (a.ctr->overflow) return;
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long total = (long long)vb.n_views * a.n;
-    if (r >= total) return;
-    int2 ext = a.ext[r];
-    if (ext.x <= 0) return;
-    int v = (int)(r / a.n);
-    unsigned g = (unsigned)(r - (long long)v * a.n);
-    const ViewInfo &vi = vb.v[v];
-    float4 ra = a.rec[r].a;
-    float z = a.rec[r].b.z;
-    float u = ra.x, vv = ra.y;
-    float x0 = ceilf(__fsub_rn(u, (float)ext.x)), x1 = floorf(__fadd_rn(u, (float)ext.x));
-    float y0 = ceilf(__fsub_rn(vv, (float)ext.y)), y1 = floorf(__fadd_rn(vv, (float)ext.y));
-    int tx0 = (x0 > 0.f ? (int)x0 : 0) / vb.tile_w;
-    int tx1 = (x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1) / vb.tile_w;
-    int ty0 = (y0 > 0.f ? (int)y0 : 0) / vb.tile_h;
-    int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
-    unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | g;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            unsigned pos = atomicAdd(a.cursor + vi.tile_base + ty * vi.tiles_x + tx, 1u);
-            if (pos < a.key_capacity) a.keys[pos] = key;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)vb.n_views * a.n;
+    unsigned cnt = 0, origin = 0, ntx = 1, tiles_x = 0;
+    unsigned long long key = 0;
+    if (r < total) {
+        const int2 ext = a.ext[r];
+        if (ext.x > 0) {
+            const int v = (int)(r / a.n);
+            const unsigned g = (unsigned)(r - (long long)v * a.n);
+            const ViewInfo &vi = vb.v[v];
+            const float4 ra = a.rec[r].a;
+            const float z = a.rec[r].b.z;
+            const float x0 = ceilf(__fsub_rn(ra.x, (float)ext.x)), x1 = floorf(__fadd_rn(ra.x, (float)ext.x));
+            const float y0 = ceilf(__fsub_rn(ra.y, (float)ext.y)), y1 = floorf(__fadd_rn(ra.y, (float)ext.y));
+            const int tx0 = (x0 > 0.f ? (int)x0 : 0) / vb.tile_w;
+            const int tx1 = (x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1) / vb.tile_w;
+            const int ty0 = (y0 > 0.f ? (int)y0 : 0) / vb.tile_h;
+            const int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
+            ntx = (unsigned)(tx1 - tx0 + 1);
+            cnt = ntx * (unsigned)(ty1 - ty0 + 1);
+            origin = (unsigned)(vi.tile_base + ty0 * vi.tiles_x + tx0);
+            tiles_x = (unsigned)vi.tiles_x;
+            key = ((unsigned long long)__float_as_uint(z) << 32) | g;
         }
+    }
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    if (wtotal == 0) return;
+    s_incl[warp][lane] = incl;
+    s_excl[warp][lane] = incl - cnt;
+    s_origin[warp][lane] = origin;
+    s_ntx[warp][lane] = ntx;
+    s_tx[warp][lane] = tiles_x;
+    s_key[warp][lane] = key;
+    __syncwarp();
+    for (unsigned base = 0; base < wtotal; base += 4 * 32) {
+        unsigned pos[4];
+        unsigned long long kk[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned j = base + u * 32 + lane;
+            pos[u] = 0xffffffffu;
+            if (j < wtotal) {
+                unsigned src = 0;
+#pragma unroll
+                for (unsigned b = 16; b > 0; b >>= 1)
+                    if (s_incl[warp][src + b - 1] <= j) src += b;
+                const unsigned local = j - s_excl[warp][src];
+                const unsigned nx = s_ntx[warp][src];
+                const unsigned tile = s_origin[warp][src] + (local / nx) * s_tx[warp][src] + (local % nx);
+                pos[u] = atomicAdd(a.cursor + tile, 1u);
+                kk[u] = s_key[warp][src];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (pos[u] < a.key_capacity) a.keys[pos[u]] = kk[u];
+    }
 }
 
 // ---- per-tile sort ----

@@ -1,36 +1,45 @@
 // Per-tile front-to-back compositing (Sec. 3.1 Eq. 2, Sec. 3.2.1 Eq. 3-5) and its
 // back-to-front backward (Sec. 3.2.2, Eq. 11).
 //
-// One CTA owns one tile (one thread per pixel). Projected Gaussians of the
-// tile's depth-sorted list are staged in shared memory in batches; a batch
-// load is skipped once every pixel of the tile has stopped (block-wide vote).
-// With a persistent grid the CTAs pull tiles, heaviest first, from a work
-// counter, which removes the tail of heavy-tailed tile loads.
+// One CTA owns one tile; each thread owns P pixels of it (the same column, rows
+// TH/P apart), so that staged-Gaussian loads, loop control and - in the
+// backward - the warp reduction of the per-Gaussian gradient are shared by P
+// pixels. Projected Gaussians of the tile's depth-sorted list are staged in
+// shared memory in batches; a batch load is skipped once every pixel of the
+// tile has stopped (block-wide vote). With a persistent grid the CTAs pull
+// tiles, heaviest first, from a work counter, which removes the tail of
+// heavy-tailed tile loads.
 #include "s3gs_internal.cuh"
 
 namespace s3gs {
 namespace {
 
+// Pixel p of this thread: column t % TW, row t / TW + p * TH / P of tile t.
+template <int TW, int TH, int P>
 struct TileCoord {
     int v;
-    int i, j;
-    bool inside;
-    long long pix;  // packed pixel index of (i, j) within view v
+    int i, j[P];
+    bool inside[P];
+    long long pix[P];  // packed pixel index within view v
     int HW;
 };
 
-template <int TW, int TH>
-__device__ __forceinline__ TileCoord tile_coord(const ViewBatch &vb, int t) {
-    TileCoord c;
+template <int TW, int TH, int P>
+__device__ __forceinline__ TileCoord<TW, TH, P> tile_coord(const ViewBatch &vb, int t) {
+    static_assert(TH % P == 0 && (TW * TH / P) % 32 == 0, "tile rows must split evenly into whole warps");
+    TileCoord<TW, TH, P> c;
     c.v = view_of_tile(vb, t);
     const ViewInfo &vi = vb.v[c.v];
-    int tl = t - vi.tile_base;
-    int ty = tl / vi.tiles_x, tx = tl - ty * vi.tiles_x;
+    const int tl = t - vi.tile_base;
+    const int ty = tl / vi.tiles_x, tx = tl - ty * vi.tiles_x;
     c.i = tx * TW + (int)(threadIdx.x % TW);
-    c.j = ty * TH + (int)(threadIdx.x / TW);
-    c.inside = c.i < vi.w && c.j < vi.h;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        c.j[p] = ty * TH + (int)(threadIdx.x / TW) + p * (TH / P);
+        c.inside[p] = c.i < vi.w && c.j[p] < vi.h;
+        c.pix[p] = (long long)c.j[p] * vi.w + c.i;
+    }
     c.HW = vi.w * vi.h;
-    c.pix = (long long)c.j * vi.w + c.i;
     return c;
 }
 
@@ -46,181 +55,265 @@ __device__ __forceinline__ int next_tile(const BlendArgs &a, const ViewBatch &vb
     return a.order ? (int)a.order[w] : w;
 }
 
-__device__ __forceinline__ void stage(const BlendArgs &a, long long rbase, unsigned b, unsigned cnt, float2 *s_xy,
-                                      float4 *s_con, float4 *s_col, unsigned *s_g) {
+// Stage list entries [b, b + cnt) of a tile into shared memory.
+__device__ __forceinline__ void stage(const BlendArgs &a, long long rbase, unsigned b, unsigned cnt, float4 *s_p0,
+                                      float4 *s_p1, float4 *s_col, unsigned *s_g) {
     for (unsigned k = threadIdx.x; k < cnt; k += blockDim.x) {
-        unsigned g = (unsigned)a.keys[b + k];
-        const Record *r = a.rec + rbase + g;
-        float4 ra = r->a, rb = r->b, rc = r->c;
-        s_xy[k] = make_float2(ra.x, ra.y);
-        s_con[k] = make_float4(ra.z, ra.w, rb.x, rb.y);
-        if (s_col) s_col[k] = make_float4(rc.x, rc.y, rc.z, rb.z);
+        const unsigned g = (unsigned)a.keys[b + k];
+        const Record r = a.rec[rbase + g];
+        const StagedGauss sg = stage_record(r);
+        s_p0[k] = make_float4(sg.u, sg.v, sg.a, sg.b);
+        s_p1[k] = make_float4(sg.c, sg.lo2, sg.o, sg.z);
+        if (s_col) s_col[k] = r.c;
         if (s_g) s_g[k] = g;
     }
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) blend_fwd_kernel(const BlendArgs a, const __grid_constant__ ViewBatch vb) {
-    constexpr int NT = TW * TH;
+// Warp sum of 10 per-lane values as a reduce-scatter: each butterfly level
+// halves the number of values a lane carries (10 -> 5 -> 3 -> 2 -> 1 -> 1), so
+// the whole reduction takes 12 shuffles instead of 50. Afterwards the even
+// lanes (lane & 1 == 0) whose code below is >= 0 own one distinct slot each;
+// the return value is that slot (or -1) and *sum its warp total.
+__device__ __forceinline__ int warp_reduce_scatter10(const float v[kGrad2d], float *sum) {
+    const unsigned lane = threadIdx.x & 31u;
+    const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u, b1 = lane & 2u;
+    float a5[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float send = b4 ? v[i] : v[i + 5];
+        const float keep = b4 ? v[i + 5] : v[i];
+        a5[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float c3[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float hi = j < 2 ? a5[3 + j] : 0.f;
+        const float send = b3 ? a5[j] : hi;
+        const float keep = b3 ? hi : a5[j];
+        c3[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float d2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float hi = j == 0 ? c3[2] : 0.f;
+        const float send = b2 ? c3[j] : hi;
+        const float keep = b2 ? hi : c3[j];
+        d2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float e = (b1 ? d2[1] : d2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? d2[0] : d2[1], 2);
+    e += __shfl_xor_sync(0xffffffffu, e, 1);
+    *sum = e;
+    int slot;
+    if (!b3) slot = b2 ? (b1 ? -1 : 2) : (b1 ? 1 : 0);
+    else slot = b2 ? -1 : (b1 ? 4 : 3);
+    if ((lane & 1u) || slot < 0) return -1;
+    return slot + (b4 ? 5 : 0);
+}
+
+template <int TW, int TH, int P, bool COUNT>
+__global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a, const __grid_constant__ ViewBatch vb) {
+    constexpr int NT = TW * TH / P;
     extern __shared__ float4 smem[];
     __shared__ int s_tile;
     const unsigned B = (unsigned)a.batch;
-    float4 *s_con = smem;
-    float4 *s_col = smem + B;
-    float2 *s_xy = reinterpret_cast<float2 *>(smem + 2 * B);
+    float4 *s_p0 = smem;
+    float4 *s_p1 = smem + B;
+    float4 *s_col = smem + 2 * B;
     if (a.ctr->overflow) return;
     unsigned long long n_proc = 0, n_blend = 0;
     for (int iter = 0;; ++iter) {
-        int t = next_tile(a, vb, &a.ctr->work_fwd, iter, &s_tile);
+        const int t = next_tile(a, vb, &a.ctr->work_fwd, iter, &s_tile);
         if (t < 0) break;
-        TileCoord c = tile_coord<TW, TH>(vb, t);
+        const TileCoord<TW, TH, P> c = tile_coord<TW, TH, P>(vb, t);
         const ViewInfo &vi = vb.v[c.v];
         const long long rbase = (long long)c.v * a.n;
-        const float px = (float)c.i, py = (float)c.j;
+        const float px = (float)c.i;
         const unsigned s = a.tile_start[t], e = a.tile_start[t + 1];
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-        unsigned last = 0;
-        bool done = !c.inside;
+        float T[P], C0[P], C1[P], C2[P], D[P];
+        unsigned last[P];
+        bool done[P];
+        bool all_done = true;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            T[p] = 1.f; C0[p] = C1[p] = C2[p] = D[p] = 0.f; last[p] = 0;
+            done[p] = !c.inside[p];
+            all_done = all_done && done[p];
+        }
         for (unsigned b = s; b < e; b += B) {
-            if (__syncthreads_count(done) == NT) break;
-            unsigned cnt = min(B, e - b);
-            stage(a, rbase, b, cnt, s_xy, s_con, s_col, nullptr);
+            if (__syncthreads_count(all_done) == NT) break;
+            const unsigned cnt = min(B, e - b);
+            stage(a, rbase, b, cnt, s_p0, s_p1, s_col, nullptr);
             __syncthreads();
-            if (!done) {
-                for (unsigned k = 0; k < cnt; ++k) {
-                    float2 xy = s_xy[k];
-                    float4 cn = s_con[k];
-                    PairEval pe = eval_pair(px, py, xy.x, xy.y, cn.x, cn.y, cn.z, cn.w);
-                    if (a.counting) ++n_proc;
+            for (unsigned k = 0; k < cnt && !all_done; ++k) {
+                const float4 p0 = s_p0[k], p1 = s_p1[k];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (done[p]) continue;
+                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, p1.x, p1.y);
+                    if (COUNT) ++n_proc;
                     if (!pe.pass) continue;
-                    float Tn = next_T(T, pe.alpha);
+                    const float al = pair_alpha(pe);
+                    const float Tn = next_T(T[p], al);
                     if (Tn < kTMin) {
-                        done = true;
-                        break;
+                        done[p] = true;
+                        continue;
                     }
-                    float w = pe.alpha * T;
-                    float4 cz = s_col[k];
-                    C0 = fmaf(cz.x, w, C0);
-                    C1 = fmaf(cz.y, w, C1);
-                    C2 = fmaf(cz.z, w, C2);
-                    D = fmaf(cz.w, w, D);
-                    T = Tn;
-                    last = b - s + k + 1;
-                    if (a.counting) ++n_blend;
+                    const float w = al * T[p];
+                    const float4 col = s_col[k];
+                    C0[p] = fmaf(col.x, w, C0[p]);
+                    C1[p] = fmaf(col.y, w, C1[p]);
+                    C2[p] = fmaf(col.z, w, C2[p]);
+                    D[p] = fmaf(p1.w, w, D[p]);
+                    T[p] = Tn;
+                    last[p] = b - s + k + 1;
+                    if (COUNT) ++n_blend;
                 }
+                all_done = true;
+#pragma unroll
+                for (int p = 0; p < P; ++p) all_done = all_done && done[p];
             }
         }
-        if (c.inside) {
-            const long long p1 = vi.pix_base + c.pix;
-            const long long p3 = 3 * vi.pix_base + c.pix;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (!c.inside[p]) continue;
+            const long long q1 = vi.pix_base + c.pix[p];
+            const long long q3 = 3 * vi.pix_base + c.pix[p];
             if (a.rgb) {
-                a.rgb[p3] = C0 + T * a.bg[0];
-                a.rgb[p3 + c.HW] = C1 + T * a.bg[1];
-                a.rgb[p3 + 2 * c.HW] = C2 + T * a.bg[2];
+                a.rgb[q3] = C0[p] + T[p] * a.bg[0];
+                a.rgb[q3 + c.HW] = C1[p] + T[p] * a.bg[1];
+                a.rgb[q3 + 2 * c.HW] = C2[p] + T[p] * a.bg[2];
             }
-            if (a.depth) a.depth[p1] = D;
-            if (a.alpha) a.alpha[p1] = 1.f - T;
+            if (a.depth) a.depth[q1] = D[p];
+            if (a.alpha) a.alpha[q1] = 1.f - T[p];
             if (a.pointmap) {
                 // Eq. 5: X^r = ((i - cx) D / fx, (j - cy) D / fy, D)
-                a.pointmap[p3] = (px - vi.cx) / vi.fx * D;
-                a.pointmap[p3 + c.HW] = (py - vi.cy) / vi.fy * D;
-                a.pointmap[p3 + 2 * c.HW] = D;
+                a.pointmap[q3] = (px - vi.cx) / vi.fx * D[p];
+                a.pointmap[q3 + c.HW] = ((float)c.j[p] - vi.cy) / vi.fy * D[p];
+                a.pointmap[q3 + 2 * c.HW] = D[p];
             }
             if (a.T_final) {
-                a.T_final[p1] = T;
-                a.n_last[p1] = last;
+                a.T_final[q1] = T[p];
+                a.n_last[q1] = last[p];
             }
         }
     }
-    if (a.counting) {
+    if (COUNT) {
         atomicAdd(&a.ctr->fwd_processed, n_proc);
         atomicAdd(&a.ctr->fwd_blended, n_blend);
     }
 }
 
-template <int TW, int TH, bool RECOMPUTE, bool DET>
-__global__ void __launch_bounds__(TW *TH) blend_bwd_kernel(const BlendArgs a, const __grid_constant__ ViewBatch vb) {
-    constexpr int NT = TW * TH;
+template <int TW, int TH, int P, bool RECOMPUTE, bool DET, bool COUNT>
+__global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a, const __grid_constant__ ViewBatch vb) {
+    constexpr int NT = TW * TH / P;
     constexpr int NW = NT / 32;
     extern __shared__ float4 smem[];
     __shared__ int s_tile;
     __shared__ unsigned s_maxlast;
     const unsigned B = (unsigned)a.batch;
-    float4 *s_con = smem;
-    float4 *s_col = smem + B;
-    float2 *s_xy = reinterpret_cast<float2 *>(smem + 2 * B);
-    unsigned *s_g = reinterpret_cast<unsigned *>(s_xy + B);
+    float4 *s_p0 = smem;
+    float4 *s_p1 = smem + B;
+    float4 *s_col = smem + 2 * B;
+    unsigned *s_g = reinterpret_cast<unsigned *>(smem + 3 * B);
     float *s_part = reinterpret_cast<float *>(s_g + B);  // DET: [NW][B][10]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (a.ctr->overflow) return;
     unsigned long long n_proc = 0;
     for (int iter = 0;; ++iter) {
-        int t = next_tile(a, vb, &a.ctr->work_bwd, iter, &s_tile);
+        const int t = next_tile(a, vb, &a.ctr->work_bwd, iter, &s_tile);
         if (t < 0) break;
-        TileCoord c = tile_coord<TW, TH>(vb, t);
+        const TileCoord<TW, TH, P> c = tile_coord<TW, TH, P>(vb, t);
         const ViewInfo &vi = vb.v[c.v];
         const long long rbase = (long long)c.v * a.n;
-        const float px = (float)c.i, py = (float)c.j;
+        const float px = (float)c.i;
         const unsigned s = a.tile_start[t], e = a.tile_start[t + 1];
-        const long long p1 = vi.pix_base + c.pix;
-        const long long p3 = 3 * vi.pix_base + c.pix;
 
         // per-pixel blend state: stored by the forward, or replayed here
-        float T = 1.f;
-        unsigned last = 0;
+        float T[P];
+        unsigned last[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            T[p] = 1.f;
+            last[p] = 0;
+        }
         if (RECOMPUTE) {
-            bool done = !c.inside;
+            bool done[P];
+            bool all_done = true;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                done[p] = !c.inside[p];
+                all_done = all_done && done[p];
+            }
             for (unsigned b = s; b < e; b += B) {
-                if (__syncthreads_count(done) == NT) break;
-                unsigned cnt = min(B, e - b);
-                stage(a, rbase, b, cnt, s_xy, s_con, nullptr, nullptr);
+                if (__syncthreads_count(all_done) == NT) break;
+                const unsigned cnt = min(B, e - b);
+                stage(a, rbase, b, cnt, s_p0, s_p1, nullptr, nullptr);
                 __syncthreads();
-                if (!done) {
-                    for (unsigned k = 0; k < cnt; ++k) {
-                        float2 xy = s_xy[k];
-                        float4 cn = s_con[k];
-                        PairEval pe = eval_pair(px, py, xy.x, xy.y, cn.x, cn.y, cn.z, cn.w);
+                for (unsigned k = 0; k < cnt && !all_done; ++k) {
+                    const float4 p0 = s_p0[k], q1 = s_p1[k];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        if (done[p]) continue;
+                        const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y);
                         if (!pe.pass) continue;
-                        float Tn = next_T(T, pe.alpha);
+                        const float Tn = next_T(T[p], pair_alpha(pe));
                         if (Tn < kTMin) {
-                            done = true;
-                            break;
+                            done[p] = true;
+                            continue;
                         }
-                        T = Tn;
-                        last = b - s + k + 1;
+                        T[p] = Tn;
+                        last[p] = b - s + k + 1;
                     }
+                    all_done = true;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) all_done = all_done && done[p];
                 }
             }
             __syncthreads();
-        } else if (c.inside) {
-            T = a.T_final[p1];
-            last = a.n_last[p1];
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                if (c.inside[p]) {
+                    T[p] = a.T_final[vi.pix_base + c.pix[p]];
+                    last[p] = a.n_last[vi.pix_base + c.pix[p]];
+                }
         }
 
         // upstream gradients; the pointmap (Eq. 5) is linear in D
-        float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gT = 0.f;
-        if (c.inside) {
-            if (a.d_rgb) {
-                gC0 = a.d_rgb[p3];
-                gC1 = a.d_rgb[p3 + c.HW];
-                gC2 = a.d_rgb[p3 + 2 * c.HW];
+        float gC0[P], gC1[P], gC2[P], gD[P], Bacc[P];
+        unsigned mylast = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            gC0[p] = gC1[p] = gC2[p] = gD[p] = 0.f;
+            float gT = 0.f;
+            if (c.inside[p]) {
+                const long long q1 = vi.pix_base + c.pix[p];
+                const long long q3 = 3 * vi.pix_base + c.pix[p];
+                if (a.d_rgb) {
+                    gC0[p] = a.d_rgb[q3];
+                    gC1[p] = a.d_rgb[q3 + c.HW];
+                    gC2[p] = a.d_rgb[q3 + 2 * c.HW];
+                }
+                if (a.d_depth) gD[p] = a.d_depth[q1];
+                if (a.d_pointmap) {
+                    gD[p] += (px - vi.cx) / vi.fx * a.d_pointmap[q3] +
+                             ((float)c.j[p] - vi.cy) / vi.fy * a.d_pointmap[q3 + c.HW] + a.d_pointmap[q3 + 2 * c.HW];
+                }
+                gT = a.bg[0] * gC0[p] + a.bg[1] * gC1[p] + a.bg[2] * gC2[p];
+                if (a.d_alpha) gT -= a.d_alpha[q1];
+            } else {
+                last[p] = 0;
             }
-            if (a.d_depth) gD = a.d_depth[p1];
-            if (a.d_pointmap) {
-                gD += (px - vi.cx) / vi.fx * a.d_pointmap[p3] + (py - vi.cy) / vi.fy * a.d_pointmap[p3 + c.HW] +
-                      a.d_pointmap[p3 + 2 * c.HW];
-            }
-            gT = a.bg[0] * gC0 + a.bg[1] * gC1 + a.bg[2] * gC2;
-            if (a.d_alpha) gT -= a.d_alpha[p1];
-        } else {
-            last = 0;
+            Bacc[p] = gT;  // gradient-weighted value of everything behind the current Gaussian
+            mylast = max(mylast, last[p]);
         }
 
         if (threadIdx.x == 0) s_maxlast = 0;
         __syncthreads();
-        if (last) atomicMax(&s_maxlast, last);
+        if (mylast) atomicMax(&s_maxlast, mylast);
         __syncthreads();
         const unsigned maxlast = s_maxlast;
+        const unsigned wmaxlast = __reduce_max_sync(0xffffffffu, mylast);  // this warp's last list entry
         if (DET) {
             // duplicates never reached by any pixel carry a zero partial
             for (unsigned k = s + maxlast + threadIdx.x; k < e; k += NT)
@@ -228,84 +321,79 @@ __global__ void __launch_bounds__(TW *TH) blend_bwd_kernel(const BlendArgs a, co
                 for (int q = 0; q < kGrad2d; ++q) a.det_partial[(long long)k * kGrad2d + q] = 0.f;
         }
 
-        float Bacc = gT;  // gradient-weighted value of everything behind the current Gaussian
         for (unsigned bend = s + maxlast; bend > s;) {
-            unsigned bstart = (bend - s > B) ? bend - B : s;
-            unsigned cnt = bend - bstart;
+            const unsigned bstart = (bend - s > B) ? bend - B : s;
+            const unsigned cnt = bend - bstart;
             __syncthreads();
-            stage(a, rbase, bstart, cnt, s_xy, s_con, s_col, s_g);
+            stage(a, rbase, bstart, cnt, s_p0, s_p1, s_col, s_g);
             __syncthreads();
             for (int k = (int)cnt - 1; k >= 0; --k) {
-                unsigned pos = bstart - s + (unsigned)k;
+                const unsigned pos = bstart - s + (unsigned)k;
+                if (pos >= wmaxlast) {
+                    // no pixel of this warp reaches the entry: its partial is zero
+                    if (DET && lane < kGrad2d) s_part[((size_t)warp * B + k) * kGrad2d + lane] = 0.f;
+                    continue;
+                }
                 float vals[kGrad2d];
 #pragma unroll
                 for (int q = 0; q < kGrad2d; ++q) vals[q] = 0.f;
                 bool contrib = false;
-                if (pos < last) {
-                    float2 xy = s_xy[k];
-                    float4 cn = s_con[k];
-                    PairEval pe = eval_pair(px, py, xy.x, xy.y, cn.x, cn.y, cn.z, cn.w);
-                    if (a.counting) ++n_proc;
-                    if (pe.pass) {
-                        contrib = true;
-                        const float al = pe.alpha;
-                        const float Tk = __fdiv_rn(T, __fsub_rn(1.f, al));  // T before this Gaussian
-                        const float w = al * Tk;
-                        const float4 cz = s_col[k];
-                        const float f = cz.x * gC0 + cz.y * gC1 + cz.z * gC2 + cz.w * gD;
-                        const float da = Tk * (f - Bacc);
-                        Bacc = f * al + (1.f - al) * Bacc;
-                        T = Tk;
-                        vals[kGR] = w * gC0;
-                        vals[kGG] = w * gC1;
-                        vals[kGBl] = w * gC2;
-                        vals[kGZ] = w * gD;
-                        if (!pe.clamped) {
-                            // alpha = o exp(-q/2): d/do = G, d/dq = -alpha/2
-                            vals[kGO] = da * pe.G;
-                            const float dq = -0.5f * da * al;
-                            vals[kGA] = dq * pe.dx * pe.dx;
-                            vals[kGB] = 2.f * dq * pe.dx * pe.dy;
-                            vals[kGC] = dq * pe.dy * pe.dy;
-                            // dx = i - u, dy = j - v
-                            vals[kGU] = -2.f * dq * (cn.x * pe.dx + cn.y * pe.dy);
-                            vals[kGV] = -2.f * dq * (cn.y * pe.dx + cn.z * pe.dy);
-                        }
+                const float4 p0 = s_p0[k], q1 = s_p1[k];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (pos >= last[p]) continue;
+                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y);
+                    if (COUNT) ++n_proc;
+                    if (!pe.pass) continue;
+                    contrib = true;
+                    // Gradient terms of one pair, with explicit rounding so that every
+                    // instantiation (stored or recomputed state, any schedule) computes
+                    // the same bits and deterministic mode is reproducible across them.
+                    const float al = pair_alpha(pe);
+                    const float om = __fsub_rn(1.f, al);
+                    const float Tk = __fdividef(T[p], om);  // T in front of this Gaussian
+                    const float w = __fmul_rn(al, Tk);
+                    const float4 col = s_col[k];
+                    const float f = __fmaf_rn(col.x, gC0[p], __fmaf_rn(col.y, gC1[p],
+                                              __fmaf_rn(col.z, gC2[p], __fmul_rn(q1.w, gD[p]))));
+                    const float da = __fmul_rn(Tk, __fsub_rn(f, Bacc[p]));
+                    Bacc[p] = __fmaf_rn(f, al, __fmul_rn(om, Bacc[p]));
+                    T[p] = Tk;
+                    vals[kGR] = __fmaf_rn(w, gC0[p], vals[kGR]);
+                    vals[kGG] = __fmaf_rn(w, gC1[p], vals[kGG]);
+                    vals[kGBl] = __fmaf_rn(w, gC2[p], vals[kGBl]);
+                    vals[kGZ] = __fmaf_rn(w, gD[p], vals[kGZ]);
+                    if (!pe.clamped) {
+                        // alpha = 2^(p + log2 o): d alpha / d logit = alpha (1 - o),
+                        // d alpha / dp = alpha ln 2, with p quadratic in (dx, dy) and dx = i - u
+                        const float g = __fmul_rn(da, al);
+                        const float ngl = __fmul_rn(-kLn2, g);
+                        const float hg = __fmul_rn(-0.5f, g);
+                        vals[kGO] = __fmaf_rn(g, __fsub_rn(1.f, q1.z), vals[kGO]);
+                        vals[kGA] = __fmaf_rn(__fmul_rn(hg, pe.dx), pe.dx, vals[kGA]);
+                        vals[kGB] = __fmaf_rn(__fmul_rn(-g, pe.dx), pe.dy, vals[kGB]);
+                        vals[kGC] = __fmaf_rn(__fmul_rn(hg, pe.dy), pe.dy, vals[kGC]);
+                        const float tu = __fmaf_rn(__fmul_rn(2.f, p0.z), pe.dx, __fmul_rn(p0.w, pe.dy));
+                        const float tv = __fmaf_rn(p0.w, pe.dx, __fmul_rn(__fmul_rn(2.f, q1.x), pe.dy));
+                        vals[kGU] = __fmaf_rn(ngl, tu, vals[kGU]);
+                        vals[kGV] = __fmaf_rn(ngl, tv, vals[kGV]);
                     }
                 }
                 if (DET) {
-#pragma unroll
-                    for (int q = 0; q < kGrad2d; ++q) {
-                        float x = vals[q];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        vals[q] = x;
-                    }
-                    if (lane == 0) {
-                        float *dst = s_part + ((size_t)warp * B + k) * kGrad2d;
-#pragma unroll
-                        for (int q = 0; q < kGrad2d; ++q) dst[q] = vals[q];
-                    }
+                    float sum;
+                    const int slot = warp_reduce_scatter10(vals, &sum);
+                    if (slot >= 0) s_part[((size_t)warp * B + k) * kGrad2d + slot] = sum;
                 } else if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                    for (int q = 0; q < kGrad2d; ++q) {
-                        float x = vals[q];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        vals[q] = x;
-                    }
-                    if (lane == 0) {
-                        float *dst = a.grad2d + (rbase + s_g[k]) * kGrad2d;
-#pragma unroll
-                        for (int q = 0; q < kGrad2d; ++q) atomicAdd(dst + q, vals[q]);
-                    }
+                    float sum;
+                    const int slot = warp_reduce_scatter10(vals, &sum);
+                    if (slot >= 0) atomicAdd(a.grad2d + (rbase + s_g[k]) * kGrad2d + slot, sum);
                 }
             }
             if (DET) {
                 __syncthreads();
                 // per-duplicate partial: warps summed in a fixed order
                 for (unsigned idx = threadIdx.x; idx < cnt * kGrad2d; idx += NT) {
-                    unsigned k = idx / kGrad2d, q = idx % kGrad2d;
+                    const unsigned k = idx / kGrad2d, q = idx % kGrad2d;
                     float x = 0.f;
 #pragma unroll
                     for (int wv = 0; wv < NW; ++wv) x += s_part[((size_t)wv * B + k) * kGrad2d + q];
@@ -315,16 +403,14 @@ __global__ void __launch_bounds__(TW *TH) blend_bwd_kernel(const BlendArgs a, co
             bend = bstart;
         }
     }
-    if (a.counting) atomicAdd(&a.ctr->bwd_processed, n_proc);
+    if (COUNT) atomicAdd(&a.ctr->bwd_processed, n_proc);
 }
 
-template <int TW, int TH>
-size_t fwd_smem(int batch) { return (size_t)batch * (2 * sizeof(float4) + sizeof(float2)); }
+size_t fwd_smem(int batch) { return (size_t)batch * (3 * sizeof(float4)); }
 
-template <int TW, int TH, bool DET>
-size_t bwd_smem(int batch) {
-    size_t s = (size_t)batch * (2 * sizeof(float4) + sizeof(float2) + sizeof(unsigned));
-    if (DET) s += (size_t)(TW * TH / 32) * batch * kGrad2d * sizeof(float);
+size_t bwd_smem(int batch, int n_warps, bool det) {
+    size_t s = (size_t)batch * (3 * sizeof(float4) + sizeof(unsigned));
+    if (det) s += (size_t)n_warps * batch * kGrad2d * sizeof(float);
     return s;
 }
 
@@ -338,57 +424,81 @@ cudaError_t ensure_smem(K kernel, size_t bytes, int *cached) {
     return e;
 }
 
-template <int TW, int TH>
-cudaError_t fwd_impl(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    static int cached = 48 * 1024;
-    size_t sm = fwd_smem<TW, TH>(a.batch);
-    auto k = blend_fwd_kernel<TW, TH>;
+template <int TW, int TH, int P, bool C>
+cudaError_t fwd_impl3(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    static int cached = 0;
+    const size_t sm = fwd_smem(a.batch);
+    auto k = blend_fwd_kernel<TW, TH, P, C>;
     cudaError_t e = ensure_smem(k, sm, &cached);
     if (e != cudaSuccess) return e;
-    k<<<grid, TW * TH, sm, s>>>(a, vb);
+    k<<<grid, TW * TH / P, sm, s>>>(a, vb);
     return cudaGetLastError();
 }
 
-template <int TW, int TH, bool R, bool D>
+template <int TW, int TH, int P>
+cudaError_t fwd_impl2(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    return a.counting ? fwd_impl3<TW, TH, P, true>(a, vb, grid, s) : fwd_impl3<TW, TH, P, false>(a, vb, grid, s);
+}
+
+template <int TW, int TH, int P, bool R, bool D, bool C>
+cudaError_t bwd_impl4(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    static int cached = 0;
+    const size_t sm = bwd_smem(a.batch, TW * TH / P / 32, D);
+    auto k = blend_bwd_kernel<TW, TH, P, R, D, C>;
+    cudaError_t e = ensure_smem(k, sm, &cached);
+    if (e != cudaSuccess) return e;
+    k<<<grid, TW * TH / P, sm, s>>>(a, vb);
+    return cudaGetLastError();
+}
+
+template <int TW, int TH, int P, bool R, bool D>
+cudaError_t bwd_impl3(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    return a.counting ? bwd_impl4<TW, TH, P, R, D, true>(a, vb, grid, s)
+                      : bwd_impl4<TW, TH, P, R, D, false>(a, vb, grid, s);
+}
+
+template <int TW, int TH, int P>
 cudaError_t bwd_impl2(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    static int cached = 48 * 1024;
-    size_t sm = bwd_smem<TW, TH, D>(a.batch);
-    auto k = blend_bwd_kernel<TW, TH, R, D>;
-    cudaError_t e = ensure_smem(k, sm, &cached);
-    if (e != cudaSuccess) return e;
-    k<<<grid, TW * TH, sm, s>>>(a, vb);
-    return cudaGetLastError();
+    const bool R = a.T_final == nullptr, D = a.det_partial != nullptr;
+    if (R && D) return bwd_impl3<TW, TH, P, true, true>(a, vb, grid, s);
+    if (R) return bwd_impl3<TW, TH, P, true, false>(a, vb, grid, s);
+    if (D) return bwd_impl3<TW, TH, P, false, true>(a, vb, grid, s);
+    return bwd_impl3<TW, TH, P, false, false>(a, vb, grid, s);
 }
 
-template <int TW, int TH>
-cudaError_t bwd_impl(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    const bool R = a.T_final == nullptr, D = a.det_partial != nullptr;
-    if (R && D) return bwd_impl2<TW, TH, true, true>(a, vb, grid, s);
-    if (R) return bwd_impl2<TW, TH, true, false>(a, vb, grid, s);
-    if (D) return bwd_impl2<TW, TH, false, true>(a, vb, grid, s);
-    return bwd_impl2<TW, TH, false, false>(a, vb, grid, s);
+// Tile shape x pixels per thread, for the forward (F = true) or the backward.
+template <bool F, int TW, int TH>
+cudaError_t by_ppt(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    switch (a.ppt) {
+    case 1: return F ? fwd_impl2<TW, TH, 1>(a, vb, grid, s) : bwd_impl2<TW, TH, 1>(a, vb, grid, s);
+    case 2: return F ? fwd_impl2<TW, TH, 2>(a, vb, grid, s) : bwd_impl2<TW, TH, 2>(a, vb, grid, s);
+    case 4:
+        if constexpr ((TW * TH / 4) % 32 == 0)
+            return F ? fwd_impl2<TW, TH, 4>(a, vb, grid, s) : bwd_impl2<TW, TH, 4>(a, vb, grid, s);
+        return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool F>
+cudaError_t dispatch(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    if (grid <= 0) return cudaSuccess;
+    const int tw = vb.tile_w, th = vb.tile_h;
+    if (tw == 16 && th == 16) return by_ppt<F, 16, 16>(a, vb, grid, s);
+    if (tw == 16 && th == 8) return by_ppt<F, 16, 8>(a, vb, grid, s);
+    if (tw == 8 && th == 8) return by_ppt<F, 8, 8>(a, vb, grid, s);
+    if (tw == 32 && th == 8) return by_ppt<F, 32, 8>(a, vb, grid, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 cudaError_t launch_blend_fwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    if (grid <= 0) return cudaSuccess;
-    const int tw = vb.tile_w, th = vb.tile_h;
-    if (tw == 16 && th == 16) return fwd_impl<16, 16>(a, vb, grid, s);
-    if (tw == 16 && th == 8) return fwd_impl<16, 8>(a, vb, grid, s);
-    if (tw == 8 && th == 8) return fwd_impl<8, 8>(a, vb, grid, s);
-    if (tw == 32 && th == 8) return fwd_impl<32, 8>(a, vb, grid, s);
-    return cudaErrorInvalidValue;
+    return dispatch<true>(a, vb, grid, s);
 }
 
 cudaError_t launch_blend_bwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    if (grid <= 0) return cudaSuccess;
-    const int tw = vb.tile_w, th = vb.tile_h;
-    if (tw == 16 && th == 16) return bwd_impl<16, 16>(a, vb, grid, s);
-    if (tw == 16 && th == 8) return bwd_impl<16, 8>(a, vb, grid, s);
-    if (tw == 8 && th == 8) return bwd_impl<8, 8>(a, vb, grid, s);
-    if (tw == 32 && th == 8) return bwd_impl<32, 8>(a, vb, grid, s);
-    return cudaErrorInvalidValue;
+    return dispatch<false>(a, vb, grid, s);
 }
 
 }  // namespace s3gs

@@ -183,8 +183,14 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
             float vv = vi.fy * py * iz + vi.cy;
             if (det > 0.f && isfinite(u) && isfinite(vv)) {
                 float idet = 1.0f / det;
-                // integer half-extents of the 3-sigma ellipse's bounding box
-                float ex = ceilf(3.0f * sqrtf(ca)), ey = ceilf(3.0f * sqrtf(cc));
+                // Integer half-extents of the 3-sigma ellipse's bounding box, widened
+                // by a margin that covers FP32 rounding of the conic: its error grows
+                // with the condition number of the 2D covariance.
+                const float mid = 0.5f * (ca + cc);
+                const float disc = sqrtf(fmaxf(mid * mid - det, 0.0f));
+                const float kappa = (mid + disc) / fmaxf(mid - disc, 1e-6f);
+                const float widen = 1.0f + 1e-5f + 4e-7f * kappa;
+                float ex = ceilf(3.0f * sqrtf(ca) * widen + 0.01f), ey = ceilf(3.0f * sqrtf(cc) * widen + 0.01f);
                 int rx = ex < (float)kExtentMax ? (int)ex : kExtentMax;
                 int ry = ey < (float)kExtentMax ? (int)ey : kExtentMax;
                 float x0 = ceilf(__fsub_rn(u, (float)rx)), x1 = floorf(__fadd_rn(u, (float)rx));
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                     }
                     Record R;
                     R.a = make_float4(u, vv, cc * idet, -cb * idet);
-                    R.b = make_float4(ca * idet, A.opacity, pz, 0.f);
+                    R.b = make_float4(ca * idet, A.opacity, pz, log2f(A.opacity));
                     R.c = make_float4(col[0], col[1], col[2], 0.f);
                     a.rec[r] = R;
                     ext = make_int2(rx, ry);
@@ -258,137 +264,162 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
 #pragma unroll
     for (int i = 0; i < NC * 3; ++i) dk[i] = 0.f;
 
-    for (int v = 0; v < vb.n_views; ++v) {
-        const ViewInfo &vi = vb.v[v];
-        long long r = (long long)v * a.n + gg;
-        float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        int2 ext = ok ? a.ext[r] : make_int2(0, 0);
-        if (ext.x > 0) {
-            float gr[kGrad2d];
-            float *gp = a.grad2d + r * kGrad2d;
+    // Views are processed in chunks: the extents, then the 2D-gradient rows of a
+    // chunk are all requested before any is used, so their latencies overlap.
+    constexpr int CH = D >= 2 ? 2 : 4;
+    for (int v0 = 0; v0 < vb.n_views; v0 += CH) {
+        int2 ext4[CH];
 #pragma unroll
-            for (int i = 0; i < kGrad2d; ++i) gr[i] = gp[i];
+        for (int u = 0; u < CH; ++u) {
+            const int v = v0 + u;
+            ext4[u] = (ok && v < vb.n_views) ? a.ext[(long long)v * a.n + gg] : make_int2(0, 0);
+        }
+        float gr4[CH][kGrad2d];
 #pragma unroll
-            for (int i = 0; i < kGrad2d; ++i) gp[i] = 0.f;  // leave the accumulator clean
-            float T[12];
-            load_pose(vi, a.Tdev, v, T);
-            float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
-            float py = T[4] * m[0] + T[5] * m[1] + T[6] * m[2] + T[7];
-            float pz = T[8] * m[0] + T[9] * m[1] + T[10] * m[2] + T[11];
-            float Sc[9];
-            cam_cov(T, A.Sig, Sc);
-            float iz = 1.0f / pz, iz2 = iz * iz;
-            float fx = vi.fx, fy = vi.fy;
-            float j00 = fx * iz, j02 = -fx * px * iz2, j11 = fy * iz, j12 = -fy * py * iz2;
-            float ca = j00 * (j00 * Sc[0] + j02 * Sc[2]) + j02 * (j00 * Sc[6] + j02 * Sc[8]) + kDilation;
-            float cb = j11 * (j00 * Sc[1] + j02 * Sc[7]) + j12 * (j00 * Sc[2] + j02 * Sc[8]);
-            float cc = j11 * (j11 * Sc[4] + j12 * Sc[5]) + j12 * (j11 * Sc[7] + j12 * Sc[8]) + kDilation;
-            float idet = 1.0f / (ca * cc - cb * cb);
-            float cA = cc * idet, cB = -cb * idet, cC = ca * idet;
-            // conic -> 2D covariance: G2 = -Sinv Ginv Sinv, Ginv = [[gA, gB/2], [gB/2, gC]]
-            float hB = 0.5f * gr[kGB];
-            float t00 = cA * gr[kGA] + cB * hB, t01 = cA * hB + cB * gr[kGC];
-            float t10 = cB * gr[kGA] + cC * hB, t11 = cB * hB + cC * gr[kGC];
-            float g00 = -(t00 * cA + t01 * cB);
-            float g01 = -(t00 * cB + t01 * cC);
-            float g11 = -(t10 * cB + t11 * cC);
-            // cov2 = J Sc J^T: dSc = J^T G2 J, dJ = 2 G2 J Sc
-            float P0[3] = {g00 * j00, g01 * j11, g00 * j02 + g01 * j12};  // row 0 of G2 J
-            float P1[3] = {g01 * j00, g11 * j11, g01 * j02 + g11 * j12};  // row 1 of G2 J
-            float Gc[9];
-            const float J0[3] = {j00, 0.f, j02}, J1[3] = {0.f, j11, j12};
+        for (int u = 0; u < CH; ++u) {
+            const float2 *src = reinterpret_cast<const float2 *>(a.grad2d + ((long long)(v0 + u) * a.n + gg) * kGrad2d);
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < kGrad2d / 2; ++i) {
+                const float2 x = ext4[u].x > 0 ? src[i] : make_float2(0.f, 0.f);
+                gr4[u][2 * i] = x.x;
+                gr4[u][2 * i + 1] = x.y;
+            }
+        }
 #pragma unroll
-                for (int j = 0; j < 3; ++j) Gc[3 * i + j] = J0[i] * P0[j] + J1[i] * P1[j];
-            float dJ00 = 2.f * (P0[0] * Sc[0] + P0[1] * Sc[3] + P0[2] * Sc[6]);
-            float dJ02 = 2.f * (P0[0] * Sc[2] + P0[1] * Sc[5] + P0[2] * Sc[8]);
-            float dJ11 = 2.f * (P1[0] * Sc[1] + P1[1] * Sc[4] + P1[2] * Sc[7]);
-            float dJ12 = 2.f * (P1[0] * Sc[2] + P1[1] * Sc[5] + P1[2] * Sc[8]);
-            // Sc = W Sig W^T: dSig += W^T Gc W
-            float GW[9];
+        for (int u = 0; u < CH; ++u)
+            if (ext4[u].x > 0) {  // leave the accumulator clean for the next backward
+                float2 *dst = reinterpret_cast<float2 *>(a.grad2d + ((long long)(v0 + u) * a.n + gg) * kGrad2d);
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < kGrad2d / 2; ++i) dst[i] = make_float2(0.f, 0.f);
+            }
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    GW[3 * i + j] = Gc[3 * i] * T[j] + Gc[3 * i + 1] * T[4 + j] + Gc[3 * i + 2] * T[8 + j];
-            {
-                float WG[9];
+        for (int u = 0; u < CH; ++u) {
+            const int v = v0 + u;
+            if (v >= vb.n_views) break;
+            const ViewInfo &vi = vb.v[v];
+            float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (ext4[u].x > 0) {
+                const float *gr = gr4[u];
+                float T[12];
+                load_pose(vi, a.Tdev, v, T);
+                float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
+                float py = T[4] * m[0] + T[5] * m[1] + T[6] * m[2] + T[7];
+                float pz = T[8] * m[0] + T[9] * m[1] + T[10] * m[2] + T[11];
+                float Sc[9];
+                cam_cov(T, A.Sig, Sc);
+                float iz = 1.0f / pz, iz2 = iz * iz;
+                float fx = vi.fx, fy = vi.fy;
+                float j00 = fx * iz, j02 = -fx * px * iz2, j11 = fy * iz, j12 = -fy * py * iz2;
+                float ca = j00 * (j00 * Sc[0] + j02 * Sc[2]) + j02 * (j00 * Sc[6] + j02 * Sc[8]) + kDilation;
+                float cb = j11 * (j00 * Sc[1] + j02 * Sc[7]) + j12 * (j00 * Sc[2] + j02 * Sc[8]);
+                float cc = j11 * (j11 * Sc[4] + j12 * Sc[5]) + j12 * (j11 * Sc[7] + j12 * Sc[8]) + kDilation;
+                float idet = 1.0f / (ca * cc - cb * cb);
+                float cA = cc * idet, cB = -cb * idet, cC = ca * idet;
+                // conic -> 2D covariance: G2 = -Sinv Ginv Sinv, Ginv = [[gA, gB/2], [gB/2, gC]]
+                float hB = 0.5f * gr[kGB];
+                float t00 = cA * gr[kGA] + cB * hB, t01 = cA * hB + cB * gr[kGC];
+                float t10 = cB * gr[kGA] + cC * hB, t11 = cB * hB + cC * gr[kGC];
+                float g00 = -(t00 * cA + t01 * cB);
+                float g01 = -(t00 * cB + t01 * cC);
+                float g11 = -(t10 * cB + t11 * cC);
+                // cov2 = J Sc J^T: dSc = J^T G2 J, dJ = 2 G2 J Sc
+                float P0[3] = {g00 * j00, g01 * j11, g00 * j02 + g01 * j12};  // row 0 of G2 J
+                float P1[3] = {g01 * j00, g11 * j11, g01 * j02 + g11 * j12};  // row 1 of G2 J
+                float Gc[9];
+                const float J0[3] = {j00, 0.f, j02}, J1[3] = {0.f, j11, j12};
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) Gc[3 * i + j] = J0[i] * P0[j] + J1[i] * P1[j];
+                float dJ00 = 2.f * (P0[0] * Sc[0] + P0[1] * Sc[3] + P0[2] * Sc[6]);
+                float dJ02 = 2.f * (P0[0] * Sc[2] + P0[1] * Sc[5] + P0[2] * Sc[8]);
+                float dJ11 = 2.f * (P1[0] * Sc[1] + P1[1] * Sc[4] + P1[2] * Sc[7]);
+                float dJ12 = 2.f * (P1[0] * Sc[2] + P1[1] * Sc[5] + P1[2] * Sc[8]);
+                // Sc = W Sig W^T: dSig += W^T Gc W
+                float GW[9];
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
-                        WG[3 * i + j] = T[i] * GW[j] + T[4 + i] * GW[3 + j] + T[8 + i] * GW[6 + j];
-                dSig[0] += WG[0]; dSig[1] += WG[1]; dSig[2] += WG[2];
-                dSig[3] += WG[4]; dSig[4] += WG[5]; dSig[5] += WG[8];
-            }
-            // camera-frame mean
-            float dp0 = gr[kGU] * fx * iz - dJ02 * fx * iz2;
-            float dp1 = gr[kGV] * fy * iz - dJ12 * fy * iz2;
-            float dp2 = -gr[kGU] * fx * px * iz2 - gr[kGV] * fy * py * iz2 + gr[kGZ] - dJ00 * fx * iz2 +
-                        2.f * dJ02 * fx * px * iz2 * iz - dJ11 * fy * iz2 + 2.f * dJ12 * fy * py * iz2 * iz;
-            dmu[0] += T[0] * dp0 + T[4] * dp1 + T[8] * dp2;
-            dmu[1] += T[1] * dp0 + T[5] * dp1 + T[9] * dp2;
-            dmu[2] += T[2] * dp0 + T[6] * dp1 + T[10] * dp2;
-            // twist: dp = rho + phi x p; dSc = [phi]x Sc - Sc [phi]x
-            tw[0] = dp0; tw[1] = dp1; tw[2] = dp2;
-            tw[3] = py * dp2 - pz * dp1;
-            tw[4] = pz * dp0 - px * dp2;
-            tw[5] = px * dp1 - py * dp0;
-            // Q = Sc Gc - Gc Sc; dphi += 2 (Q12, Q20, Q01)
-            float Q12 = 0.f, Q20 = 0.f, Q01 = 0.f;
+                        GW[3 * i + j] = Gc[3 * i] * T[j] + Gc[3 * i + 1] * T[4 + j] + Gc[3 * i + 2] * T[8 + j];
+                {
+                    float WG[9];
 #pragma unroll
-            for (int kk = 0; kk < 3; ++kk) {
-                Q12 += Sc[3 + kk] * Gc[3 * kk + 2] - Gc[3 + kk] * Sc[3 * kk + 2];
-                Q20 += Sc[6 + kk] * Gc[3 * kk + 0] - Gc[6 + kk] * Sc[3 * kk + 0];
-                Q01 += Sc[0 + kk] * Gc[3 * kk + 1] - Gc[0 + kk] * Sc[3 * kk + 1];
-            }
-            tw[3] += 2.f * Q12; tw[4] += 2.f * Q20; tw[5] += 2.f * Q01;
-            dO += gr[kGO];
-            // colour
-            if (D == 0) {
-                dk[0] += gr[kGR]; dk[1] += gr[kGG]; dk[2] += gr[kGBl];
-            } else {
-                float C[3];
-                cam_centre(T, C);
-                float ddx = m[0] - C[0], ddy = m[1] - C[1], ddz = m[2] - C[2];
-                float in = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
-                float hx = ddx * in, hy = ddy * in, hz = ddz * in;
-                float Y[16];
-                sh_basis<D>(hx, hy, hz, Y);
-                float gcol[3] = {gr[kGR], gr[kGG], gr[kGBl]};
+                    for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    float c = k[ch];
-#pragma unroll
-                    for (int i = 1; i < NC; ++i) c += Y[i] * k[3 * i + ch];
-                    if (!(c > 0.f)) gcol[ch] = 0.f;  // clamped at zero
+                        for (int j = 0; j < 3; ++j)
+                            WG[3 * i + j] = T[i] * GW[j] + T[4 + i] * GW[3 + j] + T[8 + i] * GW[6 + j];
+                    dSig[0] += WG[0]; dSig[1] += WG[1]; dSig[2] += WG[2];
+                    dSig[3] += WG[4]; dSig[4] += WG[5]; dSig[5] += WG[8];
                 }
-                float w[16];
+                // camera-frame mean
+                float dp0 = gr[kGU] * fx * iz - dJ02 * fx * iz2;
+                float dp1 = gr[kGV] * fy * iz - dJ12 * fy * iz2;
+                float dp2 = -gr[kGU] * fx * px * iz2 - gr[kGV] * fy * py * iz2 + gr[kGZ] - dJ00 * fx * iz2 +
+                            2.f * dJ02 * fx * px * iz2 * iz - dJ11 * fy * iz2 + 2.f * dJ12 * fy * py * iz2 * iz;
+                dmu[0] += T[0] * dp0 + T[4] * dp1 + T[8] * dp2;
+                dmu[1] += T[1] * dp0 + T[5] * dp1 + T[9] * dp2;
+                dmu[2] += T[2] * dp0 + T[6] * dp1 + T[10] * dp2;
+                // twist: dp = rho + phi x p; dSc = [phi]x Sc - Sc [phi]x
+                tw[0] = dp0; tw[1] = dp1; tw[2] = dp2;
+                tw[3] = py * dp2 - pz * dp1;
+                tw[4] = pz * dp0 - px * dp2;
+                tw[5] = px * dp1 - py * dp0;
+                // Q = Sc Gc - Gc Sc; dphi += 2 (Q12, Q20, Q01)
+                float Q12 = 0.f, Q20 = 0.f, Q01 = 0.f;
 #pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    dk[3 * i] += Y[i] * gcol[0];
-                    dk[3 * i + 1] += Y[i] * gcol[1];
-                    dk[3 * i + 2] += Y[i] * gcol[2];
-                    w[i] = gcol[0] * k[3 * i] + gcol[1] * k[3 * i + 1] + gcol[2] * k[3 * i + 2];
+                for (int kk = 0; kk < 3; ++kk) {
+                    Q12 += Sc[3 + kk] * Gc[3 * kk + 2] - Gc[3 + kk] * Sc[3 * kk + 2];
+                    Q20 += Sc[6 + kk] * Gc[3 * kk + 0] - Gc[6 + kk] * Sc[3 * kk + 0];
+                    Q01 += Sc[0 + kk] * Gc[3 * kk + 1] - Gc[0 + kk] * Sc[3 * kk + 1];
                 }
-                float3 gh = sh_weighted_grad<D>(hx, hy, hz, w);
-                float dd = gh.x * hx + gh.y * hy + gh.z * hz;
-                float dx_ = (gh.x - hx * dd) * in, dy_ = (gh.y - hy * dd) * in, dz_ = (gh.z - hz * dd) * in;
-                dmu[0] += dx_; dmu[1] += dy_; dmu[2] += dz_;
-                // the camera centre moves by -W^T rho: d rho += W ddir
-                tw[0] += T[0] * dx_ + T[1] * dy_ + T[2] * dz_;
-                tw[1] += T[4] * dx_ + T[5] * dy_ + T[6] * dz_;
-                tw[2] += T[8] * dx_ + T[9] * dy_ + T[10] * dz_;
+                tw[3] += 2.f * Q12; tw[4] += 2.f * Q20; tw[5] += 2.f * Q01;
+                dO += gr[kGO];
+                // colour
+                if (D == 0) {
+                    dk[0] += gr[kGR]; dk[1] += gr[kGG]; dk[2] += gr[kGBl];
+                } else {
+                    float C[3];
+                    cam_centre(T, C);
+                    float ddx = m[0] - C[0], ddy = m[1] - C[1], ddz = m[2] - C[2];
+                    float in = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+                    float hx = ddx * in, hy = ddy * in, hz = ddz * in;
+                    float Y[16];
+                    sh_basis<D>(hx, hy, hz, Y);
+                    float gcol[3] = {gr[kGR], gr[kGG], gr[kGBl]};
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        float c = k[ch];
+#pragma unroll
+                        for (int i = 1; i < NC; ++i) c += Y[i] * k[3 * i + ch];
+                        if (!(c > 0.f)) gcol[ch] = 0.f;  // clamped at zero
+                    }
+                    float w[16];
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) {
+                        dk[3 * i] += Y[i] * gcol[0];
+                        dk[3 * i + 1] += Y[i] * gcol[1];
+                        dk[3 * i + 2] += Y[i] * gcol[2];
+                        w[i] = gcol[0] * k[3 * i] + gcol[1] * k[3 * i + 1] + gcol[2] * k[3 * i + 2];
+                    }
+                    float3 gh = sh_weighted_grad<D>(hx, hy, hz, w);
+                    float dd = gh.x * hx + gh.y * hy + gh.z * hz;
+                    float dx_ = (gh.x - hx * dd) * in, dy_ = (gh.y - hy * dd) * in, dz_ = (gh.z - hz * dd) * in;
+                    dmu[0] += dx_; dmu[1] += dy_; dmu[2] += dz_;
+                    // the camera centre moves by -W^T rho: d rho += W ddir
+                    tw[0] += T[0] * dx_ + T[1] * dy_ + T[2] * dz_;
+                    tw[1] += T[4] * dx_ + T[5] * dy_ + T[6] * dz_;
+                    tw[2] += T[8] * dx_ + T[9] * dy_ + T[10] * dz_;
+                }
             }
-        }
-        // warp reduce the twist contributions of this view (fixed order)
+            // warp reduce the twist contributions of this view (fixed order)
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            float x = tw[i];
+            for (int i = 0; i < 6; ++i) {
+                float x = tw[i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) s_tw[warp][v][i] = x;
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) s_tw[warp][v][i] = x;
+            }
         }
     }
 
@@ -423,7 +454,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
         float dqq[4] = {(dq[0] - w * dot) * A.qinv, (dq[1] - x * dot) * A.qinv, (dq[2] - y * dot) * A.qinv,
                         (dq[3] - z * dot) * A.qinv};
         float dls[3] = {ds[0] * A.s[0], ds[1] * A.s[1], ds[2] * A.s[2]};
-        float dol = dO * A.opacity * (1.f - A.opacity);
+        float dol = dO;  // the blend backward accumulates dL/d(opacity logit) directly
         const bool acc = a.accumulate != 0;
         if (a.d_means) {
             float *o = a.d_means + 3 * g;

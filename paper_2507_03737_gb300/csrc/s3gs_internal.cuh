@@ -30,7 +30,7 @@ constexpr float kTMin = 1e-4f;
 constexpr int kExtentMax = 1 << 24;  // clamp of the integer half-extent of a tile cover
 constexpr int kGrad2d = 10;          // per-record 2D gradient slots
 
-// 2D gradient slot order of a record.
+// 2D gradient slot order of a record (slot kGO holds dL/d(opacity logit)).
 enum { kGU = 0, kGV, kGA, kGB, kGC, kGO, kGR, kGG, kGBl, kGZ };
 
 struct ViewInfo {
@@ -54,7 +54,7 @@ struct ViewBatch {
 // One projected (view, Gaussian) record: 48 bytes, read as three float4.
 struct __align__(16) Record {
     float4 a;  // u, v, A, B  (conic = [[A, B], [B, C]])
-    float4 b;  // C, opacity, z, unused
+    float4 b;  // C, opacity, z, log2(opacity)
     float4 c;  // r, g, b, unused
 };
 
@@ -85,30 +85,69 @@ __device__ __forceinline__ int view_of_tile(const ViewBatch &vb, int t) {
     return v;
 }
 
-// Per-pair quantities shared by the forward, the recompute replay and the
-// backward. Explicit round-to-nearest intrinsics keep the three bit-identical,
-// so that the backward takes exactly the forward's cutoff/skip/stop decisions.
+// Per-pair evaluation shared by the forward, the recompute replay and the
+// backward. A staged Gaussian carries its conic pre-scaled into the log2 domain
+// (a = -log2(e)/2 A, b = -log2(e) B, c = -log2(e)/2 C) and log2 of its opacity,
+// so that p = a dx^2 + b dx dy + c dy^2 = -log2(e) q / 2 and
+// alpha = opacity * exp(-q/2) = 2^(p + log2 opacity). The 3-sigma cutoff
+// (q <= 9), the 1/255 skip and the 0.99 clamp are all decided on these
+// exponents, before any exponential is evaluated. Explicit round-to-nearest
+// intrinsics make the three callers bit-identical, so the backward takes
+// exactly the forward's cutoff/skip/stop decisions.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kCutP = -6.4921276840003355f;   // -4.5 log2(e): q <= 9
+constexpr float kSkipL = -7.9943534368588578f;  // log2(1/255)
+constexpr float kClampL = -0.0144995696951151f; // log2(0.99)
+
+struct StagedGauss {
+    float u, v, a, b;   // centre, scaled conic (xx, 2 xy)
+    float c, lo2, o, z;  // scaled conic (yy), log2 opacity, opacity, depth
+};
+
+__device__ __forceinline__ StagedGauss stage_record(const Record &r) {
+    StagedGauss g;
+    g.u = r.a.x;
+    g.v = r.a.y;
+    g.a = __fmul_rn(-0.5f * kLog2e, r.a.z);
+    g.b = __fmul_rn(-kLog2e, r.a.w);
+    g.c = __fmul_rn(-0.5f * kLog2e, r.b.x);
+    g.o = r.b.y;
+    g.z = r.b.z;
+    g.lo2 = r.b.w;
+    return g;
+}
+
 struct PairEval {
-    float dx, dy, q, G, alpha;
+    float dx, dy;
+    float l;       // p + log2(opacity): alpha = 2^l before the clamp
     bool pass;     // inside the 3-sigma ellipse and alpha >= 1/255
     bool clamped;  // alpha hit the 0.99 clamp
 };
 
-__device__ __forceinline__ PairEval eval_pair(float px, float py, float u, float v, float A, float B,
-                                              float C, float opacity) {
+__device__ __forceinline__ PairEval eval_pair(float px, float py, float u, float v, float a, float b, float c,
+                                              float lo2) {
     PairEval e;
     e.dx = __fsub_rn(px, u);
     e.dy = __fsub_rn(py, v);
-    // q = A dx^2 + 2 B dx dy + C dy^2 = dx (A dx + 2 B dy) + C dy^2
-    float t = __fmaf_rn(A, e.dx, __fmul_rn(__fmul_rn(2.0f, B), e.dy));
-    e.q = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(C, e.dy), e.dy));
-    e.G = __expf(__fmul_rn(-0.5f, e.q));
-    float a = __fmul_rn(opacity, e.G);
-    e.clamped = a >= kAlphaMax;
-    e.alpha = e.clamped ? kAlphaMax : a;
-    e.pass = (e.q <= kCutoffQ) && (e.alpha >= kAlphaMin);
+    const float t = __fmaf_rn(a, e.dx, __fmul_rn(b, e.dy));
+    const float p = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(c, e.dy), e.dy));
+    e.l = __fadd_rn(p, lo2);
+    e.pass = (p >= kCutP) && (e.l >= kSkipL);
+    e.clamped = e.l >= kClampL;
     return e;
 }
+
+// 2^x with the hardware approximation (relative error below 2^-22); every
+// exponent reaching it lies in [log2(1/255), log2(0.99)], far from denormals.
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// alpha of a passing pair
+__device__ __forceinline__ float pair_alpha(const PairEval &e) { return e.clamped ? kAlphaMax : fast_exp2(e.l); }
 
 __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }
 
@@ -181,6 +220,7 @@ struct BlendArgs {
     DevCounters *ctr;
     int persistent;     // 0: one CTA per tile
     int batch;
+    int ppt;            // pixels per thread (1, 2 or 4)
     int counting;
 };
 cudaError_t launch_blend_fwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
