@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--batch", type=int, default=0)
-    ap.add_argument("--ppt", type=int, default=0, help="pixels per blend thread (0 = library default)")
+    ap.add_argument("--ppt", type=int, default=0, help="pixels per forward-blend thread (0 = library default)")
+    ap.add_argument("--bppt", type=int, default=0, help="pixels per backward-blend thread (0 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--deterministic", type=int, default=0)
     ap.add_argument("--recompute", type=int, default=0)
@@ -175,7 +176,7 @@ def workload_config(sc, args, extra=None):
                        f"SH degree {sc.sh_degree}, batched mapping-window fwd+loss+bwd",
            "n_gaussians": sc.n, "views": len(cams), "resolutions": res, "sh_degree": sc.sh_degree,
            "loss": f"L1 rgb {W_RGB} + depth {W_DEPTH} + pointmap {W_GEO} (Eq. 17)",
-           "tile": args.tile, "batch": args.batch or 256, "pixels_per_thread": args.ppt or 2,
+           "tile": args.tile, "batch": args.batch or 256, "pixels_per_thread": [args.ppt or 2, args.bppt or 4],
            "blocks_per_sm": args.blocks_per_sm,
            "deterministic": args.deterministic, "recompute": args.recompute,
            "l2": "flushed between timed steps (256 MB write outside the step events)"}
@@ -232,6 +233,8 @@ class Workload:
             self.opt.batch = args.batch
         if args.ppt:
             self.opt.pixels_per_thread = args.ppt
+        if args.bppt:
+            self.opt.bwd_pixels_per_thread = args.bppt
         self.R = Renderer(device.index or 0, self.opt)
         self.p = self.R.upload(sc)
         P = sum(c["width"] * c["height"] for c in self.cams)

@@ -94,7 +94,9 @@ typedef struct {
  * order of atomically accumulated gradients (and nothing in deterministic mode). */
 typedef struct {
     int32_t tile_w, tile_h;  /* tile shape: 16x16 (default), 16x8, 8x8 or 32x8 */
-    int32_t pixels_per_thread; /* pixels each blend thread owns: 1, 2 or 4 (0 = 2) */
+    int32_t pixels_per_thread; /* pixels each forward-blend thread owns: 1, 2 or 4; 0 = auto
+                                  (2, or 1 where a tile would not fill whole warps) */
+    int32_t bwd_pixels_per_thread; /* the same for the backward blend; 0 = auto (4, else 2, else 1) */
     int32_t batch;           /* Gaussians staged per shared-memory batch: 0 = 256 */
     int32_t blocks_per_sm;   /* blend kernels: 0 = one CTA per tile; k > 0 = persistent grid of
                                 k CTAs per SM pulling tiles (heaviest first) from a work counter */
@@ -106,7 +108,8 @@ typedef struct {
     float bg[3];             /* background colour composited with the final transmittance */
 } s3gs_options;
 
-/* Fill *opt with the defaults (16x16 tiles, 2 pixels per thread, batches of 256,
+/* Fill *opt with the defaults (16x16 tiles, 2 / 4 pixels per forward / backward
+ * thread, batches of 256,
  * one CTA per tile, atomic gradients, stored blend state, auto_grow = 1,
  * near_z = 0.2, black background). */
 void s3gs_options_default(s3gs_options *opt);
@@ -126,8 +129,9 @@ void s3gs_state_destroy(s3gs_state *state);
 
 /* Pre-size a state so that forwards within these limits never allocate (as
  * CUDA-graph capture requires): n Gaussians, n_views views, total_pixels over
- * all views, total_tiles over all views at the smallest tile used, and
- * max_duplicates (Gaussian, tile) pairs. Synchronous. */
+ * all views, total_tiles over all views at the smallest tile used (each tile
+ * holds 256 depth buckets internally), and max_duplicates (Gaussian, tile)
+ * pairs. Synchronous. */
 s3gs_status s3gs_reserve(s3gs_ctx *ctx, s3gs_state *state, int64_t n, int32_t n_views,
                          int64_t total_pixels, int64_t total_tiles, int64_t max_duplicates);
 

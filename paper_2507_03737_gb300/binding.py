@@ -53,7 +53,7 @@ class Camera(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("pixels_per_thread", ctypes.c_int32),
+                ("pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("deterministic", ctypes.c_int32), ("recompute", ctypes.c_int32),
                 ("auto_grow", ctypes.c_int32), ("near_z", ctypes.c_float),

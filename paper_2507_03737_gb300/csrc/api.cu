@@ -165,7 +165,11 @@ bool valid_tile(int tw, int th) {
 void fill_options(const s3gs_options *in, s3gs_options &o) {
     if (in) o = *in; else s3gs_options_default(&o);
     if (o.tile_w == 0 && o.tile_h == 0) { o.tile_w = 16; o.tile_h = 16; }
-    if (o.pixels_per_thread == 0) o.pixels_per_thread = 2;
+    // automatic pixels per thread: the preferred value if the tile still fills whole warps
+    const int px = o.tile_w * o.tile_h;
+    if (o.pixels_per_thread == 0) o.pixels_per_thread = (px / 2) % 32 == 0 ? 2 : 1;
+    if (o.bwd_pixels_per_thread == 0)
+        o.bwd_pixels_per_thread = (px / 4) % 32 == 0 ? 4 : ((px / 2) % 32 == 0 ? 2 : 1);
     if (o.batch <= 0) o.batch = 256;
     if (o.near_z == 0.f) o.near_z = 0.2f;
 }
@@ -208,11 +212,12 @@ s3gs_status ensure_forward_buffers(s3gs_ctx *ctx, s3gs_state *st, long long n_re
         if ((r = grow(ctx, st->grad2d, n_rec * kGrad2d, s, "grad2d", true)) != S3GS_OK) return r;
         st->grad_clean = true;
     }
-    if ((r = grow(ctx, st->tile_count, n_tiles + 1, s, "tile_count")) != S3GS_OK) return r;
-    if ((r = grow(ctx, st->tile_start, n_tiles + 1, s, "tile_start")) != S3GS_OK) return r;
-    if ((r = grow(ctx, st->cursor, n_tiles + 1, s, "cursor")) != S3GS_OK) return r;
+    const long long n_buckets = n_tiles * kDepthBins;
+    if ((r = grow(ctx, st->tile_count, n_buckets + 1, s, "bucket_count")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->tile_start, n_buckets + 1, s, "bucket_start")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->cursor, n_buckets + 1, s, "cursor")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->order, n_tiles + 1, s, "order")) != S3GS_OK) return r;
-    if ((r = grow(ctx, st->scan_part, (n_tiles + 4095) / 4096 + 2, s, "scan_part")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->scan_part, (n_buckets + 4095) / 4096 + 2, s, "scan_part")) != S3GS_OK) return r;
     if (store) {
         if ((r = grow(ctx, st->T_final, n_pix, s, "T_final")) != S3GS_OK) return r;
         if ((r = grow(ctx, st->n_last, n_pix, s, "n_last")) != S3GS_OK) return r;
@@ -231,7 +236,8 @@ void s3gs_options_default(s3gs_options *opt) {
     memset(opt, 0, sizeof(*opt));
     opt->tile_w = 16;
     opt->tile_h = 16;
-    opt->pixels_per_thread = 2;
+    opt->pixels_per_thread = 0;
+    opt->bwd_pixels_per_thread = 0;
     opt->batch = 256;
     opt->blocks_per_sm = 0;
     opt->deterministic = 0;
@@ -374,8 +380,11 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     if (opt.batch > 1024) return fail(ctx, S3GS_E_INVALID, "render_fwd: batch must be <= 1024");
     if (opt.pixels_per_thread != 1 && opt.pixels_per_thread != 2 && opt.pixels_per_thread != 4)
         return fail(ctx, S3GS_E_INVALID, "render_fwd: pixels_per_thread must be 1, 2 or 4");
-    if ((opt.tile_w * opt.tile_h / opt.pixels_per_thread) % 32 != 0)
-        return fail(ctx, S3GS_E_INVALID, "render_fwd: tile_w * tile_h / pixels_per_thread must be a multiple of 32");
+    if (opt.bwd_pixels_per_thread != 1 && opt.bwd_pixels_per_thread != 2 && opt.bwd_pixels_per_thread != 4)
+        return fail(ctx, S3GS_E_INVALID, "render_fwd: bwd_pixels_per_thread must be 1, 2 or 4");
+    if ((opt.tile_w * opt.tile_h / opt.pixels_per_thread) % 32 != 0 ||
+        (opt.tile_w * opt.tile_h / opt.bwd_pixels_per_thread) % 32 != 0)
+        return fail(ctx, S3GS_E_INVALID, "render_fwd: tile_w * tile_h / pixels per thread must be a multiple of 32");
     if (opt.blocks_per_sm < 0 || opt.blocks_per_sm > 64)
         return fail(ctx, S3GS_E_INVALID, "render_fwd: blocks_per_sm must be in 0..64");
     if (!(opt.near_z > 0.f) || !std::isfinite(opt.near_z))
@@ -394,8 +403,9 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
         if ((r = grow(ctx, st->keys, 1 << 16, s, "keys")) != S3GS_OK) return r;
     }
     const long long T = vb.total_tiles;
+    const long long NBK = T * kDepthBins;  // (tile, depth bin) buckets
 
-    CK(cudaMemsetAsync(st->tile_count.p, 0, (size_t)(T + 1) * sizeof(unsigned), s), "memset tile_count");
+    CK(cudaMemsetAsync(st->tile_count.p, 0, (size_t)(NBK + 1) * sizeof(unsigned), s), "memset bucket counts");
     CK(cudaMemsetAsync(st->ctr, 0, sizeof(DevCounters), s), "memset counters");
 
     ProjectArgs pa;
@@ -410,7 +420,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
 
     ScanArgs sa;
     sa.tile_count = st->tile_count.p; sa.tile_start = st->tile_start.p; sa.cursor = st->cursor.p;
-    sa.partials = st->scan_part.p; sa.ctr = st->ctr; sa.n_tiles = T; sa.key_capacity = (unsigned long long)st->keys.cap;
+    sa.partials = st->scan_part.p; sa.ctr = st->ctr; sa.n_tiles = NBK; sa.key_capacity = (unsigned long long)st->keys.cap;
     {
         StageTimer tm(ctx, kStScan, s);
         CK(launch_scan(sa, s), "scan");
@@ -521,7 +531,7 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
     ba.ctr = st->ctr;
     ba.persistent = persistent;
     ba.batch = st->opt.batch;
-    ba.ppt = st->opt.pixels_per_thread;
+    ba.ppt = st->opt.bwd_pixels_per_thread;
     ba.counting = ctx->counting;
     const long long T = vb.total_tiles;
     long long grid = persistent ? std::min<long long>(T, (long long)ctx->num_sms * st->opt.blocks_per_sm) : T;
@@ -651,10 +661,17 @@ s3gs_status s3gs_debug_binning(s3gs_ctx *ctx, s3gs_state *st, uint64_t *keys, ui
     if (n_tiles) *n_tiles = T;
     if (n_dup) *n_dup = K;
     if (!keys && !values && !ranges) return S3GS_OK;
+    const long long NBK = T * kDepthBins;
+    unsigned *bsrt = (unsigned *)malloc(sizeof(unsigned) * (NBK + 1));
     unsigned *ts = (unsigned *)malloc(sizeof(unsigned) * (T + 1));
     unsigned long long *k = (unsigned long long *)malloc(sizeof(unsigned long long) * (K > 0 ? K : 1));
-    if (!ts || !k) { free(ts); free(k); return fail(ctx, S3GS_E_NOMEM, "debug_binning: host allocation"); }
-    cudaError_t err = cudaMemcpy(ts, st->tile_start.p, sizeof(unsigned) * (T + 1), cudaMemcpyDeviceToHost);
+    if (!ts || !k || !bsrt) {
+        free(ts); free(k); free(bsrt);
+        return fail(ctx, S3GS_E_NOMEM, "debug_binning: host allocation");
+    }
+    cudaError_t err = cudaMemcpy(bsrt, st->tile_start.p, sizeof(unsigned) * (NBK + 1), cudaMemcpyDeviceToHost);
+    for (long long t = 0; t <= T; ++t) ts[t] = bsrt[t * kDepthBins];
+    free(bsrt);
     if (err == cudaSuccess && K > 0) err = cudaMemcpy(k, st->keys.p, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost);
     if (err != cudaSuccess) { free(ts); free(k); return cuda_fail(ctx, err, "debug_binning"); }
     for (long long t = 0; t < T; ++t)

@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
             const int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
             ntx = (unsigned)(tx1 - tx0 + 1);
             cnt = ntx * (unsigned)(ty1 - ty0 + 1);
-            origin = (unsigned)(vi.tile_base + ty0 * vi.tiles_x + tx0);
-            tiles_x = (unsigned)vi.tiles_x;
+            origin = (unsigned)(vi.tile_base + ty0 * vi.tiles_x + tx0) * kDepthBins + (unsigned)depth_bin(z);
+            tiles_x = (unsigned)vi.tiles_x * kDepthBins;
             key = ((unsigned long long)__float_as_uint(z) << 32) | g;
         }
     }
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
                     if (s_incl[warp][src + b - 1] <= j) src += b;
                 const unsigned local = j - s_excl[warp][src];
                 const unsigned nx = s_ntx[warp][src];
-                const unsigned tile = s_origin[warp][src] + (local / nx) * s_tx[warp][src] + (local % nx);
-                pos[u] = atomicAdd(a.cursor + tile, 1u);
+                const unsigned bucket = s_origin[warp][src] + (local / nx) * s_tx[warp][src] + (local % nx) * kDepthBins;
+                pos[u] = atomicAdd(a.cursor + bucket, 1u);
                 kk[u] = s_key[warp][src];
             }
         }
@@ -194,9 +194,16 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
 // s the first step compares element i with its mirror in the block, the
 // following steps compare i with i + d for d = s/4 ... 1. Every comparator puts
 // the smaller key at the lower index, so virtual +inf padding past the end of a
-// segment never moves and comparators that reach past the end are skipped.
-constexpr int kSortThreads = 512;
+// segment never moves and comparators that reach past the end can be skipped.
+// Steps whose partner lies in the same aligned 64-key block run in registers:
+// a warp holds such a block as two keys per lane and exchanges them with warp
+// shuffles; only the longer steps go through shared memory with block barriers.
+constexpr int kSortThreads = 256;
 constexpr int kSortCap = 4096;  // keys sorted entirely in shared memory (32 KB)
+constexpr unsigned kSegKeys = 64;  // target segment length for the warp register sorts
+constexpr unsigned long long kInfKey = ~0ull;
+
+__device__ __forceinline__ unsigned ceil_log2(unsigned n) { return n <= 1 ? 0 : 32 - __clz(n - 1); }
 
 __device__ __forceinline__ void cswap(unsigned long long *k, unsigned i, unsigned j) {
     unsigned long long x = k[i], y = k[j];
@@ -206,89 +213,318 @@ __device__ __forceinline__ void cswap(unsigned long long *k, unsigned i, unsigne
     }
 }
 
-// Full network over a segment of length n <= cap held at `k` (shared or global).
-__device__ void bitonic_full(unsigned long long *k, unsigned n) {
-    for (unsigned s = 2; s < 2 * n; s <<= 1) {
-        unsigned half = s >> 1;
-        for (unsigned t = threadIdx.x; t < ((n + 1) >> 1) + half; t += blockDim.x) {
-            unsigned blk = t / half, off = t % half;
-            unsigned i = blk * s + off, j = blk * s + s - 1 - off;
-            if (j < n) cswap(k, i, j);
+__device__ __forceinline__ void cas_local(unsigned long long &lo, unsigned long long &hi) {
+    const unsigned long long a = lo < hi ? lo : hi, b = lo < hi ? hi : lo;
+    lo = a;
+    hi = b;
+}
+
+// One comparator step on a register-held 64-key block (x0, x1) = keys
+// (2 lane, 2 lane + 1). flip: partner = e ^ (2m + 1); otherwise partner = e ^ 2m
+// (or e ^ 1 when m = 0).
+__device__ __forceinline__ void reg_step(unsigned long long &x0, unsigned long long &x1, unsigned m, bool flip) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (m == 0) {
+        cas_local(x0, x1);
+        return;
+    }
+    const unsigned long long y0 = __shfl_xor_sync(0xffffffffu, flip ? x1 : x0, m);
+    const unsigned long long y1 = __shfl_xor_sync(0xffffffffu, flip ? x0 : x1, m);
+    const unsigned top = flip ? (m + 1) >> 1 : m;  // highest bit in which the two lanes differ
+    const bool lower = (lane & top) == 0;
+    x0 = lower ? (x0 < y0 ? x0 : y0) : (x0 < y0 ? y0 : x0);
+    x1 = lower ? (x1 < y1 ? x1 : y1) : (x1 < y1 ? y1 : x1);
+}
+
+// Stages s = 2 .. min(64, N) of a register-held block.
+__device__ __forceinline__ void reg_stages(unsigned long long &x0, unsigned long long &x1, unsigned lsmax) {
+    for (unsigned ls = 1; ls <= lsmax; ++ls) {
+        reg_step(x0, x1, ((1u << ls) - 1) >> 1, true);
+        for (int ld = (int)ls - 2; ld >= 0; --ld) reg_step(x0, x1, (1u << ld) >> 1, false);
+    }
+}
+
+// Cleaner steps d = 32 .. 1 of a register-held block.
+__device__ __forceinline__ void reg_cleaners(unsigned long long &x0, unsigned long long &x1) {
+    for (int ld = 5; ld >= 0; --ld) reg_step(x0, x1, (1u << ld) >> 1, false);
+}
+
+__device__ void sort_pow2_smem(unsigned long long *k, unsigned lgN) {
+    const unsigned N = 1u << lgN, lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned nblk = N >> 6;
+    const unsigned first = lgN < 6 ? lgN : 6;
+    for (unsigned b = warp; b < (nblk > 0 ? nblk : 1); b += nw) {
+        unsigned long long x0 = k[(b << 6) + 2 * lane], x1 = k[(b << 6) + 2 * lane + 1];
+        reg_stages(x0, x1, first);
+        k[(b << 6) + 2 * lane] = x0;
+        k[(b << 6) + 2 * lane + 1] = x1;
+    }
+    __syncthreads();
+    for (unsigned ls = 7; ls <= lgN; ++ls) {
+        const unsigned lh = ls - 1, half = 1u << lh;
+        for (unsigned t = threadIdx.x; t < (N >> 1); t += blockDim.x) {
+            const unsigned blk = t >> lh, off = t & (half - 1);
+            cswap(k, (blk << ls) + off, (blk << ls) + (1u << ls) - 1 - off);
         }
         __syncthreads();
-        for (unsigned d = half >> 1; d > 0; d >>= 1) {
-            for (unsigned t = threadIdx.x; t < ((n + 1) >> 1) + d; t += blockDim.x) {
-                unsigned blk = t / d, off = t % d;
-                unsigned i = blk * 2 * d + off, j = i + d;
-                if (j < n) cswap(k, i, j);
+        for (int ld = (int)ls - 2; ld >= 6; --ld) {
+            const unsigned d = 1u << ld;
+            for (unsigned t = threadIdx.x; t < (N >> 1); t += blockDim.x) {
+                const unsigned i = ((t >> ld) << (ld + 1)) + (t & (d - 1));
+                cswap(k, i, i + d);
             }
             __syncthreads();
         }
-    }
-}
-
-// Half-cleaner steps d = d0, d0/2, ..., 1 within a segment of length n.
-__device__ void bitonic_cleaners(unsigned long long *k, unsigned n, unsigned d0) {
-    for (unsigned d = d0; d > 0; d >>= 1) {
-        for (unsigned t = threadIdx.x; t < ((n + 1) >> 1) + d; t += blockDim.x) {
-            unsigned blk = t / d, off = t % d;
-            unsigned i = blk * 2 * d + off, j = i + d;
-            if (j < n) cswap(k, i, j);
+        for (unsigned b = warp; b < nblk; b += nw) {
+            unsigned long long x0 = k[(b << 6) + 2 * lane], x1 = k[(b << 6) + 2 * lane + 1];
+            reg_cleaners(x0, x1);
+            k[(b << 6) + 2 * lane] = x0;
+            k[(b << 6) + 2 * lane + 1] = x1;
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const SortArgs a) {
-    __shared__ unsigned long long s_k[kSortCap];
-    if (a.ctr->overflow) return;
-    long long t = blockIdx.x;
-    unsigned start = a.tile_start[t], end = a.tile_start[t + 1];
-    unsigned n = end - start;
-    if (n <= 1) return;
-    unsigned long long *g = a.keys + start;
-    if (n <= (unsigned)kSortCap) {
-        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) s_k[i] = g[i];
-        __syncthreads();
-        bitonic_full(s_k, n);
-        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) g[i] = s_k[i];
+
+// ---- register sort of up to 32 R keys by one warp (R keys per lane) ----
+// Key e = R lane + h. A comparator whose partner differs from e only in the low
+// log2(R) bits runs inside the lane; otherwise the partner lane is found with a
+// shuffle (flip steps also mirror h).
+__device__ __forceinline__ unsigned long long pick(bool lower, unsigned long long a, unsigned long long b) {
+    const bool gt = a > b;
+    return (gt == lower) ? b : a;  // lower: min(a, b); upper: max(a, b)
+}
+
+template <int R, int M>
+__device__ __forceinline__ void inlane_step(unsigned long long (&x)[R]) {
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const int hp = h ^ M;
+        if (hp > h) cas_local(x[h], x[hp]);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void regR_step(unsigned long long (&x)[R], unsigned m, bool flip) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (m < (unsigned)R) {
+        switch (m) {
+        case 1: inlane_step<R, 1>(x); break;
+        case 2: if constexpr (R > 2) inlane_step<R, 2>(x); break;
+        case 3: if constexpr (R > 2) inlane_step<R, 3>(x); break;
+        case 4: if constexpr (R > 4) inlane_step<R, 4>(x); break;
+        case 5: if constexpr (R > 4) inlane_step<R, 5>(x); break;
+        case 6: if constexpr (R > 4) inlane_step<R, 6>(x); break;
+        case 7: if constexpr (R > 4) inlane_step<R, 7>(x); break;
+        default: break;
+        }
         return;
     }
-    // Heavy tile: the first log2(cap) stages of the network stay inside aligned
-    // chunks of `cap` keys and run in shared memory; every later stage runs its
-    // long-distance steps in global memory and finishes each chunk in shared.
-    for (unsigned c0 = 0; c0 < n; c0 += kSortCap) {
-        unsigned m = min((unsigned)kSortCap, n - c0);
-        for (unsigned i = threadIdx.x; i < m; i += blockDim.x) s_k[i] = g[c0 + i];
+    unsigned long long y[R];
+    if (flip) {
+        const unsigned lm = (m + 1) / R - 1, top = ((m + 1) / R) >> 1;
+        const bool lower = (lane & top) == 0;
+#pragma unroll
+        for (int h = 0; h < R; ++h) y[h] = __shfl_xor_sync(0xffffffffu, x[h ^ (R - 1)], lm);
+#pragma unroll
+        for (int h = 0; h < R; ++h) x[h] = pick(lower, x[h], y[h]);
+    } else {
+        const unsigned lm = m / R;
+        const bool lower = (lane & lm) == 0;
+#pragma unroll
+        for (int h = 0; h < R; ++h) y[h] = __shfl_xor_sync(0xffffffffu, x[h], lm);
+#pragma unroll
+        for (int h = 0; h < R; ++h) x[h] = pick(lower, x[h], y[h]);
+    }
+}
+
+// Sort of one key segment of length 2 <= n <= 32 R by one warp in registers.
+template <int R>
+__device__ __forceinline__ void sort_segment_warpR(unsigned long long *g, unsigned n) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long x[R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const unsigned e = R * lane + h;
+        x[h] = e < n ? g[e] : kInfKey;
+    }
+    const unsigned lsmax = ceil_log2(n);
+    for (unsigned ls = 1; ls <= lsmax; ++ls) {
+        regR_step<R>(x, (1u << ls) - 1, true);
+        for (int ld = (int)ls - 2; ld >= 0; --ld) regR_step<R>(x, 1u << ld, false);
+    }
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const unsigned e = R * lane + h;
+        if (e < n) g[e] = x[h];
+    }
+}
+
+// Sort of one key segment of length n > 64 by the whole block (call uniformly).
+__device__ void sort_segment_block(unsigned long long *g, unsigned n, unsigned long long *s_k) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (n <= (unsigned)kSortCap) {
+        const unsigned lgN = ceil_log2(n), N = 1u << lgN;
+        for (unsigned i = threadIdx.x; i < N; i += blockDim.x) s_k[i] = i < n ? g[i] : kInfKey;
         __syncthreads();
-        bitonic_full(s_k, m);
+        sort_pow2_smem(s_k, lgN);
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) g[i] = s_k[i];
+        __syncthreads();
+        return;
+    }
+    // Heavy segment: chunks of kSortCap keys are sorted in shared memory (the
+    // first log2(kSortCap) stages stay inside them); every later stage runs its
+    // long-distance steps in global memory and finishes each chunk in shared.
+    const unsigned lgC = ceil_log2((unsigned)kSortCap);
+    for (unsigned c0 = 0; c0 < n; c0 += kSortCap) {
+        const unsigned m = min((unsigned)kSortCap, n - c0);
+        for (unsigned i = threadIdx.x; i < (unsigned)kSortCap; i += blockDim.x) s_k[i] = i < m ? g[c0 + i] : kInfKey;
+        __syncthreads();
+        sort_pow2_smem(s_k, lgC);
         for (unsigned i = threadIdx.x; i < m; i += blockDim.x) g[c0 + i] = s_k[i];
         __syncthreads();
     }
-    for (unsigned s = 2 * kSortCap; s < 2 * n; s <<= 1) {
-        unsigned half = s >> 1;
-        for (unsigned tt = threadIdx.x; tt < ((n + 1) >> 1) + half; tt += blockDim.x) {
-            unsigned blk = tt / half, off = tt % half;
-            unsigned i = blk * s + off, j = blk * s + s - 1 - off;
+    const unsigned lgN = ceil_log2(n), N = 1u << lgN;
+    for (unsigned ls = lgC + 1; ls <= lgN; ++ls) {
+        const unsigned lh = ls - 1, half = 1u << lh;
+        for (unsigned tt = threadIdx.x; tt < (N >> 1); tt += blockDim.x) {
+            const unsigned blk = tt >> lh, off = tt & (half - 1);
+            const unsigned i = (blk << ls) + off, j = (blk << ls) + (1u << ls) - 1 - off;
             if (j < n) cswap(g, i, j);
         }
         __syncthreads();
-        for (unsigned d = half >> 1; d >= (unsigned)kSortCap; d >>= 1) {
-            for (unsigned tt = threadIdx.x; tt < ((n + 1) >> 1) + d; tt += blockDim.x) {
-                unsigned blk = tt / d, off = tt % d;
-                unsigned i = blk * 2 * d + off, j = i + d;
+        for (int ld = (int)ls - 2; ld >= (int)lgC; --ld) {
+            const unsigned d = 1u << ld;
+            for (unsigned tt = threadIdx.x; tt < (N >> 1); tt += blockDim.x) {
+                const unsigned i = ((tt >> ld) << (ld + 1)) + (tt & (d - 1)), j = i + d;
                 if (j < n) cswap(g, i, j);
             }
             __syncthreads();
         }
+        // remaining cleaner steps (d < kSortCap) stay inside aligned chunks
         for (unsigned c0 = 0; c0 < n; c0 += kSortCap) {
-            unsigned m = min((unsigned)kSortCap, n - c0);
-            for (unsigned i = threadIdx.x; i < m; i += blockDim.x) s_k[i] = g[c0 + i];
+            const unsigned m = min((unsigned)kSortCap, n - c0);
+            for (unsigned i = threadIdx.x; i < (unsigned)kSortCap; i += blockDim.x) s_k[i] = i < m ? g[c0 + i] : kInfKey;
             __syncthreads();
-            bitonic_cleaners(s_k, m, kSortCap / 2);
+            for (int ld = (int)lgC - 1; ld >= 6; --ld) {
+                const unsigned d = 1u << ld;
+                for (unsigned tt = threadIdx.x; tt < (unsigned)kSortCap / 2; tt += blockDim.x) {
+                    const unsigned i = ((tt >> ld) << (ld + 1)) + (tt & (d - 1));
+                    cswap(s_k, i, i + d);
+                }
+                __syncthreads();
+            }
+            const unsigned warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (unsigned b = warp; b < (unsigned)kSortCap / 64; b += nw) {
+                unsigned long long x0 = s_k[(b << 6) + 2 * lane], x1 = s_k[(b << 6) + 2 * lane + 1];
+                reg_cleaners(x0, x1);
+                s_k[(b << 6) + 2 * lane] = x0;
+                s_k[(b << 6) + 2 * lane + 1] = x1;
+            }
+            __syncthreads();
             for (unsigned i = threadIdx.x; i < m; i += blockDim.x) g[c0 + i] = s_k[i];
             __syncthreads();
         }
+    }
+}
+
+// In-place sort of a shared-memory segment k[0, n), 64 < n, by the whole block
+// (call uniformly). Positions past n are virtual +inf keys: register blocks pad
+// with +inf and write back only real keys; shared-memory comparators past n are
+// skipped.
+__device__ void sort_segment_smem(unsigned long long *k, unsigned n) {
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned lgN = ceil_log2(n), N = 1u << lgN, nblk = (n + 63) >> 6;
+    for (unsigned b = warp; b < nblk; b += nw) {
+        const unsigned i0 = (b << 6) + 2 * lane;
+        unsigned long long x0 = i0 < n ? k[i0] : kInfKey, x1 = i0 + 1 < n ? k[i0 + 1] : kInfKey;
+        reg_stages(x0, x1, 6);
+        if (i0 < n) k[i0] = x0;
+        if (i0 + 1 < n) k[i0 + 1] = x1;
+    }
+    __syncthreads();
+    for (unsigned ls = 7; ls <= lgN; ++ls) {
+        const unsigned lh = ls - 1, half = 1u << lh;
+        for (unsigned t = threadIdx.x; t < (N >> 1); t += blockDim.x) {
+            const unsigned blk = t >> lh, off = t & (half - 1);
+            const unsigned i = (blk << ls) + off, j = (blk << ls) + (1u << ls) - 1 - off;
+            if (j < n) cswap(k, i, j);
+        }
+        __syncthreads();
+        for (int ld = (int)ls - 2; ld >= 6; --ld) {
+            const unsigned d = 1u << ld;
+            for (unsigned t = threadIdx.x; t < (N >> 1); t += blockDim.x) {
+                const unsigned i = ((t >> ld) << (ld + 1)) + (t & (d - 1)), j = i + d;
+                if (j < n) cswap(k, i, j);
+            }
+            __syncthreads();
+        }
+        for (unsigned b = warp; b < nblk; b += nw) {
+            const unsigned i0 = (b << 6) + 2 * lane;
+            unsigned long long x0 = i0 < n ? k[i0] : kInfKey, x1 = i0 + 1 < n ? k[i0 + 1] : kInfKey;
+            reg_cleaners(x0, x1);
+            if (i0 < n) k[i0] = x0;
+            if (i0 + 1 < n) k[i0 + 1] = x1;
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per tile: its depth buckets are sorted independently - buckets of up
+// to 64 keys by single warps in registers, larger ones by the whole block. A
+// tile of up to kSortCap keys is staged in shared memory with one coalesced
+// load and stored back with one coalesced store; heavier tiles sort their
+// buckets in place in global memory.
+__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const SortArgs a) {
+    __shared__ unsigned long long s_k[kSortCap];
+    __shared__ unsigned s_start[kDepthBins + 1];
+    __shared__ unsigned s_seg[kDepthBins + 1];
+    __shared__ unsigned s_warp[33];
+    if (a.ctr->overflow) return;
+    const long long t = blockIdx.x;
+    const unsigned *bs = a.tile_start + t * kDepthBins;
+    const unsigned base = bs[0], n_tile = bs[kDepthBins] - base;
+    if (n_tile <= 1) return;
+    for (int i = threadIdx.x; i <= kDepthBins; i += blockDim.x) s_start[i] = bs[i] - base;
+    const bool staged = n_tile <= (unsigned)kSortCap;
+    unsigned long long *keys = staged ? s_k : a.keys + base;
+    if (staged)
+        for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x) s_k[i] = a.keys[base + i];
+    __syncthreads();
+    // Merge consecutive buckets into segments: a new segment starts at the first
+    // bucket beginning in each window of kSegKeys keys. Keys of an earlier bucket
+    // all precede those of a later one, so sorting a segment as a whole equals
+    // sorting its buckets one by one; segments hold about kSegKeys keys, which
+    // keeps the warps' register sorts full.
+    static_assert(kSortThreads == kDepthBins, "one thread per bucket");
+    const unsigned b = threadIdx.x;
+    const unsigned flag = (b == 0) || (s_start[b] / kSegKeys != s_start[b - 1] / kSegKeys);
+    unsigned n_seg;
+    const unsigned idx = block_excl_scan(flag, s_warp, &n_seg);
+    if (flag) s_seg[idx] = s_start[b];
+    if (b == 0) s_seg[n_seg] = n_tile;
+    __syncthreads();
+    const unsigned warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    bool any_large = false;
+    for (unsigned i = warp; i < n_seg; i += nw) {
+        const unsigned n = s_seg[i + 1] - s_seg[i];
+        if (n < 2) continue;
+        if (n <= 64) sort_segment_warpR<2>(keys + s_seg[i], n);
+        else if (n <= 128) sort_segment_warpR<4>(keys + s_seg[i], n);
+        else if (n <= 256) sort_segment_warpR<8>(keys + s_seg[i], n);
+        else any_large = true;
+    }
+    if (__syncthreads_or(any_large)) {
+        for (unsigned i = 0; i < n_seg; ++i) {
+            const unsigned n = s_seg[i + 1] - s_seg[i];
+            if (n <= 256) continue;
+            if (staged) sort_segment_smem(s_k + s_seg[i], n);
+            else sort_segment_block(a.keys + base + s_seg[i], n, s_k);
+        }
+    }
+    if (staged) {
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x) a.keys[base + i] = s_k[i];
     }
 }
 
@@ -301,7 +537,7 @@ __global__ void tile_bucket_count(const OrderArgs a) {
     __syncthreads();
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_tiles;
          t += (long long)gridDim.x * blockDim.x)
-        atomicAdd(&s_c[load_bucket(a.tile_start[t + 1] - a.tile_start[t])], 1u);
+        atomicAdd(&s_c[load_bucket(a.tile_start[(t + 1) * kDepthBins] - a.tile_start[t * kDepthBins])], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i < 33; i += blockDim.x)
         if (s_c[i]) atomicAdd(&a.bucket_cnt[i], s_c[i]);
@@ -322,7 +558,7 @@ __global__ void tile_bucket_scan(const OrderArgs a) {
 __global__ void tile_bucket_scatter(const OrderArgs a) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_tiles;
          t += (long long)gridDim.x * blockDim.x) {
-        int b = load_bucket(a.tile_start[t + 1] - a.tile_start[t]);
+        int b = load_bucket(a.tile_start[(t + 1) * kDepthBins] - a.tile_start[t * kDepthBins]);
         unsigned pos = atomicAdd(&a.bucket_cnt[b], 1u);
         a.order[pos] = (unsigned)t;
     }

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
         const ViewInfo &vi = vb.v[c.v];
         const long long rbase = (long long)c.v * a.n;
         const float px = (float)c.i;
-        const unsigned s = a.tile_start[t], e = a.tile_start[t + 1];
+        const unsigned s = a.tile_start[t * kDepthBins], e = a.tile_start[(t + 1) * kDepthBins];
         float T[P], C0[P], C1[P], C2[P], D[P];
         unsigned last[P];
         bool done[P];
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
         const ViewInfo &vi = vb.v[c.v];
         const long long rbase = (long long)c.v * a.n;
         const float px = (float)c.i;
-        const unsigned s = a.tile_start[t], e = a.tile_start[t + 1];
+        const unsigned s = a.tile_start[t * kDepthBins], e = a.tile_start[(t + 1) * kDepthBins];
 
         // per-pixel blend state: stored by the forward, or replayed here
         float T[P];

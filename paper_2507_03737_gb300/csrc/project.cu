@@ -225,9 +225,10 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                     R.c = make_float4(col[0], col[1], col[2], 0.f);
                     a.rec[r] = R;
                     ext = make_int2(rx, ry);
+                    const int bin = depth_bin(pz);
                     for (int ty = ty0; ty <= ty1; ++ty)
                         for (int tx = tx0; tx <= tx1; ++tx)
-                            atomicAdd(a.tile_count + vi.tile_base + ty * vi.tiles_x + tx, 1u);
+                            atomicAdd(a.tile_count + (size_t)(vi.tile_base + ty * vi.tiles_x + tx) * kDepthBins + bin, 1u);
                 }
             }
         }

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
             int t = vi.tile_base + ty * vi.tiles_x + tx;
-            unsigned lo = a.tile_start[t], hi = a.tile_start[t + 1];
+            unsigned lo = a.tile_start[t * kDepthBins], hi = a.tile_start[(t + 1) * kDepthBins];
             while (lo < hi) {
                 unsigned mid = lo + ((hi - lo) >> 1);
                 if (a.keys[mid] < key) lo = mid + 1; else hi = mid;

@@ -30,6 +30,18 @@ constexpr float kTMin = 1e-4f;
 constexpr int kExtentMax = 1 << 24;  // clamp of the integer half-extent of a tile cover
 constexpr int kGrad2d = 10;          // per-record 2D gradient slots
 
+// Duplicates are bucketed by (tile, coarse depth bin). The bin is the exponent
+// and the top 4 mantissa bits of the float depth (16 bins per octave), offset so
+// that z = 0.2 falls in bin 0; 256 bins cover 0.2 m to about 13 km and deeper
+// keys share the last bin. The bin is monotone in depth, so a tile's buckets,
+// each sorted, concatenate to the tile's list in (depth, index) order; bucket b
+// of tile t has id t * 256 + b.
+constexpr int kDepthBins = 256;
+__device__ __forceinline__ int depth_bin(float z) {
+    const int b = (int)(__float_as_uint(z) >> 19) - 1993;
+    return b < 0 ? 0 : (b > kDepthBins - 1 ? kDepthBins - 1 : b);
+}
+
 // 2D gradient slot order of a record (slot kGO holds dL/d(opacity logit)).
 enum { kGU = 0, kGV, kGA, kGB, kGC, kGO, kGR, kGG, kGBl, kGZ };
 
@@ -165,12 +177,12 @@ struct ProjectArgs {
 cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s);
 
 struct ScanArgs {
-    const unsigned *tile_count;
-    unsigned *tile_start;  // [T + 1]
-    unsigned *cursor;      // [T]
-    unsigned *partials;    // [ceil(T / 4096) + 1]
+    const unsigned *tile_count;  // per bucket
+    unsigned *tile_start;  // [buckets + 1]
+    unsigned *cursor;      // [buckets]
+    unsigned *partials;    // [ceil(buckets / 4096) + 1]
     DevCounters *ctr;
-    long long n_tiles;
+    long long n_tiles;     // number of buckets (tiles * kDepthBins)
     unsigned long long key_capacity;
 };
 cudaError_t launch_scan(const ScanArgs &a, cudaStream_t s);
@@ -187,7 +199,7 @@ struct EmitArgs {
 cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s);
 
 struct SortArgs {
-    const unsigned *tile_start;
+    const unsigned *tile_start;  // bucket starts
     unsigned long long *keys;
     long long n_tiles;
     const DevCounters *ctr;
@@ -195,7 +207,7 @@ struct SortArgs {
 cudaError_t launch_tile_sort(const SortArgs &a, cudaStream_t s);
 
 struct OrderArgs {
-    const unsigned *tile_start;
+    const unsigned *tile_start;  // bucket starts
     unsigned *order;       // [T] tiles, heaviest first (approximate, by log2 bucket)
     unsigned *bucket_cnt;  // [33] scratch
     long long n_tiles;
@@ -205,7 +217,7 @@ cudaError_t launch_tile_order(const OrderArgs &a, cudaStream_t s);
 struct BlendArgs {
     const Record *rec;
     const unsigned long long *keys;
-    const unsigned *tile_start;
+    const unsigned *tile_start;  // bucket starts: tile t spans buckets [t * 256, (t + 1) * 256)
     const unsigned *order;  // may be NULL: natural tile order
     long long n;
     float bg[3];

@@ -166,7 +166,8 @@ def test_persistent_and_recompute_and_det(R):
     g0 = R.backward_np(ups, 2)
     outs = {}
     for name, kw in (("persistent", dict(blocks_per_sm=2)), ("recompute", dict(recompute=1)),
-                     ("ppt1", dict(pixels_per_thread=1)), ("ppt4_recompute", dict(pixels_per_thread=4, recompute=1)),
+                     ("ppt1", dict(pixels_per_thread=1, bwd_pixels_per_thread=1)),
+                     ("ppt4_recompute", dict(pixels_per_thread=4, bwd_pixels_per_thread=2, recompute=1)),
                      ("det", dict(deterministic=1)), ("det_recompute", dict(deterministic=1, recompute=1)),
                      ("det_persistent", dict(deterministic=1, blocks_per_sm=3, batch=64))):
         out = R.render_np(sc, options=_opts(**kw))
@@ -187,9 +188,11 @@ def test_persistent_and_recompute_and_det(R):
 def test_batch_size_and_tile_do_not_change_forward(R):
     sc = scenes.config_scene(1)
     base = R.render_np(sc)
-    for kw in (dict(batch=32), dict(batch=1024), dict(tile_w=8, tile_h=8, batch=17), dict(tile_w=32, tile_h=8),
+    for kw in (dict(batch=32), dict(batch=1024), dict(tile_w=8, tile_h=8, batch=17, bwd_pixels_per_thread=2),
+               dict(tile_w=32, tile_h=8),
                dict(pixels_per_thread=1), dict(pixels_per_thread=4, batch=100),
-               dict(tile_w=16, tile_h=8, pixels_per_thread=4), dict(tile_w=8, tile_h=8, pixels_per_thread=1)):
+               dict(tile_w=16, tile_h=8, pixels_per_thread=4),
+               dict(tile_w=8, tile_h=8, pixels_per_thread=1, bwd_pixels_per_thread=1)):
         out = R.render_np(sc, options=_opts(**kw))
         for k in base:
             np.testing.assert_array_equal(out[k], base[k], err_msg=str(kw))
@@ -267,6 +270,8 @@ def test_errors_are_reported(R):
             ([sc.cameras[0]] * 33, {}, B.S3GS_E_INVALID),
             (sc.cameras, dict(tile_w=12, tile_h=12), B.S3GS_E_INVALID),
             (sc.cameras, dict(tile_w=8, tile_h=8, pixels_per_thread=4), B.S3GS_E_INVALID),
+            (sc.cameras, dict(tile_w=8, tile_h=8, bwd_pixels_per_thread=4), B.S3GS_E_INVALID),
+            (sc.cameras, dict(tile_w=8, tile_h=8, pixels_per_thread=2, bwd_pixels_per_thread=8), B.S3GS_E_INVALID),
             (sc.cameras, dict(pixels_per_thread=3), B.S3GS_E_INVALID),
             ([dict(sc.cameras[0], fx=float("nan"))], {}, B.S3GS_E_INVALID),
             ([dict(sc.cameras[0], width=0)], {}, B.S3GS_E_INVALID)):
