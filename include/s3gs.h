@@ -19,7 +19,13 @@
  * min(0.99, opacity * exp(-q/2)); alpha < 1/255 is skipped; compositing stops
  * before the Gaussian that would take the transmittance below 1e-4. Pixel
  * (i, j) is column i, row j, centred at integer coordinates; depth is the
- * view-space z of each Gaussian's mean, blended without normalisation.
+ * view-space z of each Gaussian's mean, blended without normalisation. A
+ * Gaussian is projected into a view only if its mean has z > near_z and lies
+ * in the guard cone |x/z| <= G, |y/z| <= G (G = guard_slope, default 1.5): the
+ * first-order projection of the 3DGS rasteriser the paper builds on is
+ * meaningless, and its gradient ill-conditioned, far off-axis just in front of
+ * the camera. The cone depends on the mean's direction only, so a crop of a view
+ * (shifted principal point) renders exactly that window of the view.
  * Colour: SH degree 0 uses c = k0 directly (Eq. 2); degree d >= 1 uses
  * c = max(0, k0 + sum_{l=1..d, m} Y_lm(v) k_lm) with the real orthonormal
  * spherical harmonics and v the unit vector from the camera centre to the mean.
@@ -63,8 +69,9 @@ typedef enum {
 
 #define S3GS_MAX_VIEWS 32
 #define S3GS_MAX_SH_DEGREE 3
-/* Largest number of (Gaussian, tile) duplicates one call can hold (32-bit offsets). */
-#define S3GS_MAX_DUPLICATES 2147483647LL
+/* Largest number of (Gaussian, tile) duplicates one call can hold (unsigned
+ * 32-bit offsets); larger windows must be split across calls. */
+#define S3GS_MAX_DUPLICATES 4294967295LL
 
 typedef struct s3gs_ctx s3gs_ctx;
 typedef struct s3gs_state s3gs_state;
@@ -105,6 +112,7 @@ typedef struct {
     int32_t auto_grow;       /* 1: the forward synchronises once to size the duplicate buffer
                                 (not capture-safe); 0: overflow is reported as S3GS_E_CAPACITY */
     float near_z;            /* cull Gaussians with view-space z <= near_z (0 = 0.2) */
+    float guard_slope;       /* guard cone G (0 = 1.5; negative = no cone) */
     float bg[3];             /* background colour composited with the final transmittance */
 } s3gs_options;
 

@@ -14,7 +14,7 @@ import threading
 import numpy as np
 
 __all__ = ["build_oracle", "lib", "cam_rows", "project", "render_fwd", "render_bwd",
-           "bin_referee", "sh_real", "quat_to_rotmat", "num_threads", "set_num_threads",
+           "bin_referee", "sh_real", "quat_to_rotmat", "num_threads", "set_num_threads", "set_guard",
            "pixel_offsets"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -63,6 +63,7 @@ def lib():
                                          ctypes.c_int, _F, _F, _I32, _I32, _F, _U64, _U32, _I64]
             L.or_bin_referee.restype = ctypes.c_int64
             L.or_num_threads.restype = ctypes.c_int
+            L.or_set_guard.argtypes = [ctypes.c_double]
             L.or_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
@@ -89,6 +90,12 @@ def pixel_offsets(cameras):
     for c in cameras:
         off.append(off[-1] + c["width"] * c["height"])
     return off
+
+
+def set_guard(g: float) -> None:
+    """Guard-cone slope G (a Gaussian with |x/z| or |y/z| > G is not projected);
+    <= 0 disables the cone. Default 1.5, as in the library."""
+    lib().or_set_guard(float(g))
 
 
 def num_threads() -> int:

@@ -29,7 +29,14 @@
  *  - the pose perturbation is T(tau) = Exp(tau) T_cw, tau = (rho, phi), on the
  *    left (Eq. 9's composition); the twist gradient includes every path
  *    through the pose (mean, covariance, depth, SH direction);
- *  - discrete decisions (cutoff, skip, clamp, stop) have zero derivative.
+ *  - discrete decisions (cutoff, skip, clamp, stop) have zero derivative;
+ *  - the projection is limited to a guard cone, as in the 3DGS/MonoGS
+ *    rasteriser whose projection derivatives Eq. 11 relies on: a Gaussian is
+ *    not projected into a view where its mean has |x/z| > G or |y/z| > G
+ *    (default G = 1.5), nor where z <= the near plane; the first-order (EWA)
+ *    projection is meaningless far off-axis just in front of the camera. The
+ *    rule depends on the direction of the mean only, so a crop of a view (a
+ *    shifted principal point) renders exactly that window of the view.
  *
  * Parity pins: single-Gaussian closed form, partition of unity, fronto-parallel
  * plane, brute-force unsorted evaluation, symmetries, SH against scipy, the
@@ -63,6 +70,7 @@ typedef struct {
 
 typedef struct {
     int valid;
+    double cull_margin;   /* relative distance to the near-plane / guard-cone decision */
     double u, v;          /* projected mean (pixels) */
     double A, B, C;       /* conic = inverse of the 2D covariance */
     double cov[3];        /* 2D covariance a, b, c (with dilation) */
@@ -86,6 +94,12 @@ static or_cam or_read_cam(const double *c) {
         k.t[r] = c[6 + 4 * r + 3];
     }
     return k;
+}
+
+/* ---------- small helpers ---------- */
+static double or_min3(double a, double b, double c) {
+    double m = a < b ? a : b;
+    return m < c ? m : c;
 }
 
 /* ---------- small dense helpers (row-major) ---------- */
@@ -182,6 +196,10 @@ static int or_sh_index(int l, int m) { return l * l + l + m; }
 static double or_sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
 
 /* Project Gaussian g for one camera (Eq. 1 plus the EWA projection). */
+static double or_guard = 1.5; /* guard-cone slope G; <= 0 disables the cone */
+
+void or_set_guard(double g) { or_guard = g; }
+
 static void or_project_one(const double *mean, const double *log_scale, const double *quat,
                            double opacity_logit, const double *col, int sh_degree,
                            const or_cam *cam, double near_z, or_proj *P) {
@@ -202,7 +220,19 @@ static void or_project_one(const double *mean, const double *log_scale, const do
     for (int i = 0; i < 3; ++i)
         P->p[i] = cam->W[3 * i] * mean[0] + cam->W[3 * i + 1] * mean[1] + cam->W[3 * i + 2] * mean[2] + cam->t[i];
     double px = P->p[0], py = P->p[1], pz = P->p[2];
-    if (!(pz > near_z)) return;
+    /* near plane and guard cone; a Gaussian culled close to either boundary is
+     * still projected (valid = 0) so that pixels it would reach can report the
+     * small margin of that decision */
+    int culled = !(pz > near_z);
+    double cm = fabs(pz - near_z) / near_z;
+    if (or_guard > 0 && pz > 0) {
+        double sx = fabs(px / pz), sy = fabs(py / pz);
+        if (sx > or_guard || sy > or_guard) culled = 1;
+        double mx = fabs(sx - or_guard) / or_guard, my = fabs(sy - or_guard) / or_guard;
+        cm = or_min3(cm, mx, my);
+    }
+    P->cull_margin = cm;
+    if (culled && !(cm < 1e-3 && pz > 0)) return;
 
     double Wt[9], tmp[9];
     tr3(cam->W, Wt);
@@ -238,6 +268,10 @@ static void or_project_one(const double *mean, const double *log_scale, const do
     P->v = cam->fy * py / pz + cam->cy;
     P->depth = pz;
     P->opacity = or_sigmoid(opacity_logit);
+    if (culled) {
+        P->valid = -1; /* culled near a boundary: margin bookkeeping only */
+        return;
+    }
 
     /* colour */
     if (sh_degree == 0) {
@@ -283,7 +317,7 @@ int or_project(int64_t n, int sh_degree, const double *means, const double *log_
     or_project_all(n, sh_degree, means, log_scales, quats, opacity_logits, colors, &cam, near_z, P);
     for (int64_t g = 0; g < n; ++g) {
         double *o = out + 13 * g;
-        o[0] = P[g].valid; o[1] = P[g].u; o[2] = P[g].v; o[3] = P[g].A; o[4] = P[g].B; o[5] = P[g].C;
+        o[0] = P[g].valid > 0; o[1] = P[g].u; o[2] = P[g].v; o[3] = P[g].A; o[4] = P[g].B; o[5] = P[g].C;
         o[6] = P[g].opacity; o[7] = P[g].depth; o[8] = P[g].rgb[0]; o[9] = P[g].rgb[1]; o[10] = P[g].rgb[2];
         o[11] = P[g].cov[0]; o[12] = P[g].cov[2];
     }
@@ -321,6 +355,18 @@ static int64_t or_pixel_hits(const or_proj *P, int64_t n, double px, double py, 
         double G = exp(-0.5 * q);
         double araw = p->opacity * G;
         double m = fabs(q - OR_CUTOFF_Q) / OR_CUTOFF_Q;
+        if (p->valid < 0) {
+            /* culled by the near plane or the guard cone, but close to it: if it
+             * would reach this pixel, record the decision's margin */
+            double a = araw < OR_ALPHA_MAX ? araw : OR_ALPHA_MAX;
+            if (q <= OR_CUTOFF_Q && a >= OR_ALPHA_MIN) {
+                hits[cnt].z = p->depth; hits[cnt].g = g; hits[cnt].alpha = 0; hits[cnt].G = G;
+                hits[cnt].dx = dx; hits[cnt].dy = dy; hits[cnt].clamped = 0;
+                hits[cnt].real = 0; hits[cnt].margin = p->cull_margin;
+                ++cnt;
+            }
+            continue;
+        }
         if (q > OR_CUTOFF_Q) {
             /* only a near-miss with a non-negligible alpha can flip the result */
             if (p->opacity * exp(-0.5 * OR_CUTOFF_Q) >= OR_ALPHA_MIN && m < 1e-3) {
@@ -351,7 +397,7 @@ static int64_t or_pixel_hits(const or_proj *P, int64_t n, double px, double py, 
         hits[cnt].dy = dy;
         hits[cnt].clamped = araw >= OR_ALPHA_MAX;
         hits[cnt].real = 1;
-        hits[cnt].margin = or_min(m, ms);
+        hits[cnt].margin = or_min(or_min(m, ms), p->cull_margin);
         ++cnt;
     }
     qsort(hits, (size_t)cnt, sizeof(or_hit), or_hit_cmp);
@@ -678,7 +724,7 @@ int or_render_bwd(int64_t n, int sh_degree, const double *means, const double *l
         /* chain per Gaussian */
         double tw[6] = {0, 0, 0, 0, 0, 0};
         for (int64_t g = 0; g < n; ++g) {
-            if (!P[g].valid) continue;
+            if (P[g].valid <= 0) continue;
             or_chain_params(P + g, g2 + G_N * g, &cam, means + 3 * g, colors + (int64_t)3 * nc * g, sh_degree,
                             d_means ? d_means + 3 * g : NULL, d_log_scales ? d_log_scales + 3 * g : NULL,
                             d_quats ? d_quats + 4 * g : NULL, d_opacity_logits ? d_opacity_logits + g : NULL,

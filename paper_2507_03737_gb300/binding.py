@@ -56,7 +56,7 @@ class Options(ctypes.Structure):
                 ("pixels_per_thread", ctypes.c_int32), ("bwd_pixels_per_thread", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("deterministic", ctypes.c_int32), ("recompute", ctypes.c_int32),
-                ("auto_grow", ctypes.c_int32), ("near_z", ctypes.c_float),
+                ("auto_grow", ctypes.c_int32), ("near_z", ctypes.c_float), ("guard_slope", ctypes.c_float),
                 ("bg", ctypes.c_float * 3)]
 
 

@@ -172,6 +172,7 @@ void fill_options(const s3gs_options *in, s3gs_options &o) {
         o.bwd_pixels_per_thread = (px / 4) % 32 == 0 ? 4 : ((px / 2) % 32 == 0 ? 2 : 1);
     if (o.batch <= 0) o.batch = 256;
     if (o.near_z == 0.f) o.near_z = 0.2f;
+    if (o.guard_slope == 0.f) o.guard_slope = 1.5f;
 }
 
 s3gs_status plan_views(s3gs_ctx *ctx, const s3gs_camera *cams, int n_views, int tw, int th, ViewBatch &vb) {
@@ -244,6 +245,7 @@ void s3gs_options_default(s3gs_options *opt) {
     opt->recompute = 0;
     opt->auto_grow = 1;
     opt->near_z = 0.2f;
+    opt->guard_slope = 1.5f;
 }
 
 const char *s3gs_version(void) { return kVersion; }
@@ -389,6 +391,8 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
         return fail(ctx, S3GS_E_INVALID, "render_fwd: blocks_per_sm must be in 0..64");
     if (!(opt.near_z > 0.f) || !std::isfinite(opt.near_z))
         return fail(ctx, S3GS_E_INVALID, "render_fwd: near_z must be positive");
+    if (!std::isfinite(opt.guard_slope))
+        return fail(ctx, S3GS_E_INVALID, "render_fwd: guard_slope must be finite");
     cudaStream_t s = (cudaStream_t)stream_;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     ViewBatch vb;
@@ -411,7 +415,8 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     ProjectArgs pa;
     pa.means = g->means; pa.log_scales = g->log_scales; pa.quats = g->quats;
     pa.opacity_logits = g->opacity_logits; pa.colors = g->colors;
-    pa.n = n; pa.sh_degree = g->sh_degree; pa.near_z = opt.near_z; pa.Tdev = T_cw_device;
+    pa.n = n; pa.sh_degree = g->sh_degree; pa.near_z = opt.near_z; pa.guard = opt.guard_slope;
+    pa.Tdev = T_cw_device;
     pa.rec = st->rec.p; pa.ext = st->ext.p; pa.tile_count = st->tile_count.p;
     {
         StageTimer tm(ctx, kStProject, s);

@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
         float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
         float py = T[4] * m[0] + T[5] * m[1] + T[6] * m[2] + T[7];
         float pz = T[8] * m[0] + T[9] * m[1] + T[10] * m[2] + T[11];
-        if (ok && pz > a.near_z) {
+        const bool in_cone = a.guard <= 0.f || (fabsf(px) <= a.guard * pz && fabsf(py) <= a.guard * pz);
+        if (ok && pz > a.near_z && in_cone) {
             float Sc[9];
             cam_cov(T, A.Sig, Sc);
             float iz = 1.0f / pz;

@@ -169,6 +169,7 @@ struct ProjectArgs {
     long long n;
     int sh_degree;
     float near_z;
+    float guard;  // guard-cone slope; <= 0: no cone
     const float *Tdev;
     Record *rec;
     int2 *ext;

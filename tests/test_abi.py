@@ -53,7 +53,7 @@ def test_host_only_calls(lib):
 def test_binding_struct_layout_matches_header():
     from paper_2507_03737_gb300 import binding as B
     assert ctypes.sizeof(B.Camera) == 4 * (2 + 4 + 12)
-    assert ctypes.sizeof(B.Options) == 4 * (9 + 1 + 3)
+    assert ctypes.sizeof(B.Options) == 4 * (9 + 2 + 3)
     assert B.Gaussians.means.offset == 16
 
 

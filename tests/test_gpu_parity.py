@@ -352,3 +352,43 @@ def test_autograd_function_and_pose_gradient(R):
     rgb, depth, pm, alpha = render(R, q, [cam])
     (rgb.sum() + depth.sum()).backward()
     assert float(q["means"].grad.abs().sum()) > 0 and float(q["colors"].grad.abs().sum()) > 0
+
+
+def test_autotuner_picks_a_valid_schedule_that_keeps_results(R, tmp_path):
+    from paper_2507_03737_gb300 import autotune as AT
+    sc = scenes.tiny_scene(16, n=2000, width=96, height=64, n_views=2, scale=0.12)
+    p = R.upload(sc)
+    cache = str(tmp_path / "tune.json")
+    best = AT.autotune(R, p, sc.cameras, cache_path=cache, repeats=2, rounds=1)
+    assert AT._valid(best)
+    import json
+    assert AT.signature(p, sc.cameras, best) in json.load(open(cache))
+    base = R.render_np(sc)
+    tuned = R.render_np(sc, options=best)
+    for k in base:
+        np.testing.assert_array_equal(tuned[k], base[k])
+    again = AT.autotune(R, p, sc.cameras, cache_path=cache)
+    assert AT.options_to_dict(again) == AT.options_to_dict(best)
+
+
+def test_guard_cone_matches_oracle(R):
+    """Near-plane, off-axis Gaussians: culled by the guard cone (default) and rendered
+    exactly without it; both against the oracle with the same rule."""
+    rng = np.random.default_rng(17)
+    n = 40
+    means = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.4, 0.4, n), rng.uniform(0.21, 0.5, n)], 1)
+    sc = scenes.random_gaussians(rng, means, 0, np.log(0.08), 0.3)
+    sc.cameras = [scenes.camera(64, 48, 60.0, 60.0, 31.5, 23.5)]
+    try:
+        for g in (1.5, -1.0):
+            O.set_guard(g)
+            ref = O.render_fwd(sc)
+            gpu = R.render_np(sc, options=_opts(guard_slope=g))
+            compare_forward(gpu, ref, sc.cameras, max_excluded=0.05)
+            ups = upstream(sc.cameras, 5, pixel_mask(ref))
+            g_gpu = R.backward_np(ups, 1)
+            g_ref = O.render_bwd(sc, **ups)
+            for k in ("colors", "opacity_logits"):
+                assert rel_l2(g_gpu[k], g_ref[k]) < 1e-3, (g, k)
+    finally:
+        O.set_guard(1.5)

@@ -370,3 +370,20 @@ def test_backward_background_and_alpha_terms():
         flat[k] = old + h; Lp = L(); flat[k] = old - h; Lm = L(); flat[k] = old
         fd[k] = (Lp - Lm) / (2 * h)
     np.testing.assert_allclose(g["opacity_logits"], fd, rtol=1e-6, atol=1e-9)
+
+
+def test_guard_cone_culls_far_off_axis_gaussians():
+    """A Gaussian just in front of the camera, far off-axis (|x/z| = 1.6 > G = 1.5), is not
+    projected, even though its footprint covers the image; with the cone disabled it is."""
+    sc = _single(z=0.3, s=0.6, o=0.8, mu_xy=(0.48, 0.0))  # x/z = 1.6
+    try:
+        O.set_guard(1.5)
+        r = O.render_fwd(sc)
+        assert np.abs(r["alpha"]).max() == 0.0
+        O.set_guard(-1.0)
+        r = O.render_fwd(sc)
+        assert r["alpha"].max() > 0.1
+        O.set_guard(1.7)
+        assert O.render_fwd(sc)["alpha"].max() > 0.1
+    finally:
+        O.set_guard(1.5)
