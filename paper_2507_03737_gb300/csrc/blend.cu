@@ -1,8 +1,8 @@
 // Per-tile front-to-back compositing (Sec. 3.1 Eq. 2, Sec. 3.2.1 Eq. 3-5) and its
 // back-to-front backward (Sec. 3.2.2, Eq. 11).
 //
-// One CTA owns one tile; each thread owns P pixels of it (the same column, rows
-// TH/P apart), so that staged-Gaussian loads, loop control and - in the
+// One CTA owns one tile; each thread owns P pixels of it (the same column, P
+// adjacent rows), so that staged-Gaussian loads, loop control and - in the
 // backward - the warp reduction of the per-Gaussian gradient are shared by P
 // pixels. Projected Gaussians of the tile's depth-sorted list are staged in
 // shared memory in batches; a batch load is skipped once every pixel of the
@@ -14,7 +14,8 @@
 namespace s3gs {
 namespace {
 
-// Pixel p of this thread: column t % TW, row t / TW + p * TH / P of tile t.
+// Pixel p of this thread: column t % TW, row (t / TW) P + p of tile t, so a warp
+// covers a contiguous band of rows.
 template <int TW, int TH, int P>
 struct TileCoord {
     int v;
@@ -35,7 +36,7 @@ __device__ __forceinline__ TileCoord<TW, TH, P> tile_coord(const ViewBatch &vb, 
     c.i = tx * TW + (int)(threadIdx.x % TW);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        c.j[p] = ty * TH + (int)(threadIdx.x / TW) + p * (TH / P);
+        c.j[p] = ty * TH + (int)(threadIdx.x / TW) * P + p;
         c.inside[p] = c.i < vi.w && c.j[p] < vi.h;
         c.pix[p] = (long long)c.j[p] * vi.w + c.i;
     }
