@@ -67,6 +67,7 @@ struct s3gs_state {
     s3gs_ctx *ctx = nullptr;
     DevBuf<Record> rec;
     DevBuf<int2> ext;
+    DevBuf<unsigned> vis_mask;
     DevBuf<float> grad2d;
     DevBuf<unsigned> tile_count, tile_start, cursor, order, scan_part;
     DevBuf<unsigned long long> keys;
@@ -209,6 +210,7 @@ s3gs_status ensure_forward_buffers(s3gs_ctx *ctx, s3gs_state *st, long long n_re
     s3gs_status r;
     if ((r = grow(ctx, st->rec, n_rec, s, "records")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->ext, n_rec, s, "extents")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->vis_mask, n, s, "visibility")) != S3GS_OK) return r;
     if (n_rec * kGrad2d > st->grad2d.cap || !st->grad2d.p) {
         if ((r = grow(ctx, st->grad2d, n_rec * kGrad2d, s, "grad2d", true)) != S3GS_OK) return r;
         st->grad_clean = true;
@@ -336,7 +338,7 @@ void s3gs_state_destroy(s3gs_state *st) {
     if (!st) return;
     if (st->ctx) cudaSetDevice(st->ctx->device);
     cudaDeviceSynchronize();
-    void *bufs[] = {st->rec.p, st->ext.p, st->grad2d.p, st->tile_count.p, st->tile_start.p, st->cursor.p,
+    void *bufs[] = {st->rec.p, st->ext.p, st->vis_mask.p, st->grad2d.p, st->tile_count.p, st->tile_start.p, st->cursor.p,
                     st->order.p, st->scan_part.p, st->bucket, st->keys.p, st->det_partial.p, st->T_final.p,
                     st->n_last.p, st->twist_part.p, st->ctr};
     for (void *p : bufs)
@@ -417,7 +419,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     pa.opacity_logits = g->opacity_logits; pa.colors = g->colors;
     pa.n = n; pa.sh_degree = g->sh_degree; pa.near_z = opt.near_z; pa.guard = opt.guard_slope;
     pa.Tdev = T_cw_device;
-    pa.rec = st->rec.p; pa.ext = st->ext.p; pa.tile_count = st->tile_count.p;
+    pa.rec = st->rec.p; pa.ext = st->ext.p; pa.vis_mask = st->vis_mask.p; pa.tile_count = st->tile_count.p;
     {
         StageTimer tm(ctx, kStProject, s);
         CK(launch_project(pa, vb, s), "project");
@@ -556,7 +558,8 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
     ProjectBwdArgs pb;
     pb.means = st->g.means; pb.log_scales = st->g.log_scales; pb.quats = st->g.quats;
     pb.opacity_logits = st->g.opacity_logits; pb.colors = st->g.colors;
-    pb.n = n; pb.sh_degree = st->g.sh_degree; pb.Tdev = st->Tdev; pb.ext = st->ext.p; pb.grad2d = st->grad2d.p;
+    pb.n = n; pb.sh_degree = st->g.sh_degree; pb.Tdev = st->Tdev; pb.vis_mask = st->vis_mask.p;
+    pb.grad2d = st->grad2d.p;
     pb.d_means = d_means; pb.d_log_scales = d_log_scales; pb.d_quats = d_quats;
     pb.d_opacity_logits = d_opacity_logits; pb.d_colors = d_colors;
     pb.accumulate = accumulate;

@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
 #pragma unroll
     for (int i = 0; i < NC * 3; ++i) k[i] = cp[i];
 
+    unsigned mask = 0;
     for (int v = 0; v < vb.n_views; ++v) {
         const ViewInfo &vi = vb.v[v];
         long long r = (long long)v * a.n + g;
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                     R.c = make_float4(col[0], col[1], col[2], 0.f);
                     a.rec[r] = R;
                     ext = make_int2(rx, ry);
+                    mask |= 1u << v;
                     const int bin = depth_bin(pz);
                     for (int ty = ty0; ty <= ty1; ++ty)
                         for (int tx = tx0; tx <= tx1; ++tx)
@@ -235,6 +237,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
         }
         a.ext[r] = ext;
     }
+    a.vis_mask[g] = mask;
 }
 
 // Backward of the projection for every view of one Gaussian, accumulating
@@ -266,30 +269,31 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
 #pragma unroll
     for (int i = 0; i < NC * 3; ++i) dk[i] = 0.f;
 
-    // Views are processed in chunks: the extents, then the 2D-gradient rows of a
-    // chunk are all requested before any is used, so their latencies overlap.
+    // Views are processed in chunks whose 2D-gradient rows are all requested
+    // before any is used, so their latencies overlap; the visibility mask says
+    // which rows exist without reading the per-record extents.
+    const unsigned vis = ok ? a.vis_mask[gg] : 0u;
+    for (int i = threadIdx.x; i < 8 * S3GS_MAX_VIEWS * 6; i += blockDim.x) (&s_tw[0][0][0])[i] = 0.f;
+    __syncthreads();
     constexpr int CH = D >= 2 ? 2 : 4;
     for (int v0 = 0; v0 < vb.n_views; v0 += CH) {
-        int2 ext4[CH];
-#pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            const int v = v0 + u;
-            ext4[u] = (ok && v < vb.n_views) ? a.ext[(long long)v * a.n + gg] : make_int2(0, 0);
-        }
+        const unsigned chunk_any = __any_sync(0xffffffffu, (vis >> v0) & ((1u << CH) - 1u));
+        if (!chunk_any) continue;  // no Gaussian of this warp is seen by these views
         float gr4[CH][kGrad2d];
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
+            const bool seen = (v0 + u < vb.n_views) && ((vis >> (v0 + u)) & 1u);
             const float2 *src = reinterpret_cast<const float2 *>(a.grad2d + ((long long)(v0 + u) * a.n + gg) * kGrad2d);
 #pragma unroll
             for (int i = 0; i < kGrad2d / 2; ++i) {
-                const float2 x = ext4[u].x > 0 ? src[i] : make_float2(0.f, 0.f);
+                const float2 x = seen ? src[i] : make_float2(0.f, 0.f);
                 gr4[u][2 * i] = x.x;
                 gr4[u][2 * i + 1] = x.y;
             }
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            if (ext4[u].x > 0) {  // leave the accumulator clean for the next backward
+            if ((v0 + u < vb.n_views) && ((vis >> (v0 + u)) & 1u)) {  // leave the accumulator clean
                 float2 *dst = reinterpret_cast<float2 *>(a.grad2d + ((long long)(v0 + u) * a.n + gg) * kGrad2d);
 #pragma unroll
                 for (int i = 0; i < kGrad2d / 2; ++i) dst[i] = make_float2(0.f, 0.f);
@@ -299,8 +303,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
             const int v = v0 + u;
             if (v >= vb.n_views) break;
             const ViewInfo &vi = vb.v[v];
+            const bool seen = (vis >> v) & 1u;
+            if (!__any_sync(0xffffffffu, seen)) continue;
             float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (ext4[u].x > 0) {
+            if (seen) {
                 const float *gr = gr4[u];
                 float T[12];
                 load_pose(vi, a.Tdev, v, T);

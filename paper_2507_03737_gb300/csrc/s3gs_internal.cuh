@@ -173,6 +173,7 @@ struct ProjectArgs {
     const float *Tdev;
     Record *rec;
     int2 *ext;
+    unsigned *vis_mask;  // [n]: bit v set if the Gaussian is projected into view v
     unsigned *tile_count;
 };
 cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s);
@@ -255,7 +256,7 @@ struct ProjectBwdArgs {
     long long n;
     int sh_degree;
     const float *Tdev;
-    const int2 *ext;
+    const unsigned *vis_mask;
     float *grad2d;  // read, then cleared to zero for the next backward
     float *d_means, *d_log_scales, *d_quats, *d_opacity_logits, *d_colors;
     int accumulate;
