@@ -66,15 +66,16 @@ def patch_stats(X: np.ndarray, rs: slice, cs: slice):
 def align(Xr, Xp, P=10, delta_mu=0.3, delta_sigma=0.3, eps_r=0.1, max_iter=3, tau=0.01, sigma_init=1.0):
     """Algorithm 1 on one view. Returns a dict with the final scale ``sigma``, the
     per-iteration scales, |CP| and the CP mask of the last iteration, the
-    insufficiency flag, and decision margins (relative distances of every
+    insufficiency flag, decision margins (relative distances of every
     candidate test and every correct-point test from its threshold) for the
-    last iteration."""
+    last iteration, and the smallest of each kind for every iteration."""
     Xr = np.asarray(Xr, dtype=np.float64)
     Xp = np.asarray(Xp, dtype=np.float64)
     _, H, W = Xr.shape
     rows, cols = patch_grid(H, W, P)
     sigma = float(sigma_init)
     history = []
+    min_margins = []   # per iteration: smallest patch margin, smallest point margin
     cp = np.zeros((H, W), dtype=bool)
     patch_margin = np.full((len(rows), len(cols)), np.inf)
     point_margin = np.full((H, W), np.inf)
@@ -104,6 +105,7 @@ def align(Xr, Xp, P=10, delta_mu=0.3, delta_sigma=0.3, eps_r=0.1, max_iter=3, ta
                 d = np.sqrt(((nr - np_) ** 2).sum(axis=0))
                 cp[rs, cs] = d < eps_r
                 point_margin[rs, cs] = np.abs(eps_r - d) / eps_r
+        min_margins.append((float(patch_margin.min()), float(point_margin.min())))
         if cp.any():
             num = Xr[:, cp].sum()
             den = Xp[:, cp].sum()
@@ -112,7 +114,7 @@ def align(Xr, Xp, P=10, delta_mu=0.3, delta_sigma=0.3, eps_r=0.1, max_iter=3, ta
     n_cp = int(cp.sum())
     return dict(sigma=sigma, history=history, n_cp=n_cp, cp=cp,
                 insufficient=bool(n_cp < tau * H * W), patch_margin=patch_margin,
-                point_margin=point_margin)
+                point_margin=point_margin, min_margins=min_margins)
 
 
 def replace(Xr, Xp, sigma: float, eps_m=0.15):

@@ -7,7 +7,7 @@ seeded scene generators can be used without loading the CUDA library.
 """
 import importlib
 
-__all__ = ["scenes", "binding", "autograd", "autotune", "build"]
+__all__ = ["scenes", "binding", "autograd", "autotune", "build", "slam"]
 
 
 def __getattr__(name):

@@ -22,7 +22,9 @@ __all__ = [
     "s3gs_render_bwd", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_debug_records",
     "s3gs_debug_binning", "s3gs_set_counting", "s3gs_read_counters", "s3gs_version",
     "s3gs_set_timing", "s3gs_read_timing", "STAGES", "s3gs_mapping_loss_noalloc",
-    "make_cameras", "make_gaussians", "check",
+    "make_cameras", "make_gaussians", "check", "AlignParams", "s3gs_align_params_default",
+    "s3gs_scale_align_workspace", "s3gs_scale_align", "s3gs_pointmap_replace", "s3gs_scale_remedy", "view_sizes",
+    "PoseAdam", "s3gs_pose_adam_default", "s3gs_se3_exp", "s3gs_pose_update",
 ]
 
 S3GS_OK, S3GS_E_INVALID, S3GS_E_CAPACITY, S3GS_E_CUDA = 0, -1, -2, -3
@@ -58,6 +60,16 @@ class Options(ctypes.Structure):
                 ("deterministic", ctypes.c_int32), ("recompute", ctypes.c_int32),
                 ("auto_grow", ctypes.c_int32), ("near_z", ctypes.c_float), ("guard_slope", ctypes.c_float),
                 ("bg", ctypes.c_float * 3)]
+
+
+class AlignParams(ctypes.Structure):
+    _fields_ = [("patch", ctypes.c_int32), ("delta_mu", ctypes.c_float), ("delta_sigma", ctypes.c_float),
+                ("eps_r", ctypes.c_float), ("max_iter", ctypes.c_int32), ("tau", ctypes.c_float)]
+
+
+class PoseAdam(ctypes.Structure):
+    _fields_ = [("lr_rho", ctypes.c_float), ("lr_phi", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
 _P = ctypes.c_void_p
@@ -100,6 +112,19 @@ def _load():
         "s3gs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
         "s3gs_read_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
         "s3gs_version": (ctypes.c_char_p, []),
+        "s3gs_align_params_default": (None, [ctypes.POINTER(AlignParams)]),
+        "s3gs_scale_align_workspace": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32,
+                                                      ctypes.POINTER(ctypes.c_size_t)]),
+        "s3gs_scale_align": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.POINTER(AlignParams), _P, _P,
+                                            _P, _P, _P, _P, ctypes.c_size_t, _P]),
+        "s3gs_pointmap_replace": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_float, _P, _P, _P,
+                                                 _P, _P]),
+        "s3gs_scale_remedy": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64, _P,
+                                             _P, _P]),
+        "s3gs_pose_adam_default": (None, [ctypes.POINTER(PoseAdam)]),
+        "s3gs_se3_exp": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
+        "s3gs_pose_update": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(PoseAdam), _P, _P, _P, _P, _P,
+                                            _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -120,8 +145,8 @@ def _ptr(t):
         return None
     if isinstance(t, int):
         return t
-    if not t.is_cuda or t.dtype != torch.float32 and t.dtype not in (torch.int32, torch.uint32):
-        raise TypeError("expected a float32 CUDA tensor")
+    if not t.is_cuda or t.dtype not in (torch.float32, torch.int32, torch.uint32, torch.int64, torch.uint8):
+        raise TypeError("expected a float32 / int32 / int64 / uint8 CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return t.data_ptr()
@@ -293,3 +318,65 @@ def s3gs_read_counters(ctx, state):
     a = ctypes.c_int64(); b = ctypes.c_int64(); c = ctypes.c_int64()
     check(ctx, lib().s3gs_read_counters(ctx, state, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return dict(fwd_processed=a.value, fwd_blended=b.value, bwd_processed=c.value)
+
+
+def view_sizes(cameras_or_wh):
+    """Host int32 [n_views][2] (width, height) array from camera dicts or (w, h) pairs."""
+    wh = []
+    for c in cameras_or_wh:
+        wh += [int(c["width"]), int(c["height"])] if isinstance(c, dict) else [int(c[0]), int(c[1])]
+    arr = (ctypes.c_int32 * len(wh))(*wh)
+    return arr, len(wh) // 2
+
+
+def s3gs_align_params_default(**kw) -> AlignParams:
+    p = AlignParams()
+    lib().s3gs_align_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def s3gs_scale_align_workspace(view_wh, n_views, patch) -> int:
+    b = ctypes.c_size_t()
+    st = lib().s3gs_scale_align_workspace(view_wh, int(n_views), int(patch), ctypes.byref(b))
+    if st != S3GS_OK:
+        raise S3GSError(st, "scale_align_workspace: sizes out of range")
+    return b.value
+
+
+def s3gs_scale_align(ctx, view_wh, n_views, X_r, X_p, params, sigma_init, sigma, n_cp, insufficient, cp_mask,
+                     workspace, stream=None):
+    ws = workspace.numel() * workspace.element_size()
+    check(ctx, lib().s3gs_scale_align(ctx, view_wh, int(n_views), _ptr(X_r), _ptr(X_p), ctypes.byref(params),
+                                      _ptr(sigma_init), _ptr(sigma), _ptr(n_cp), _ptr(insufficient), _ptr(cp_mask),
+                                      workspace.data_ptr(), ws, _stream(stream)))
+
+
+def s3gs_pointmap_replace(ctx, view_wh, n_views, X_r, X_p, sigma, eps_m, X_r_hat, X_p_hat, replaced, n_replaced,
+                          stream=None):
+    check(ctx, lib().s3gs_pointmap_replace(ctx, view_wh, int(n_views), _ptr(X_r), _ptr(X_p), _ptr(sigma),
+                                           float(eps_m), _ptr(X_r_hat), _ptr(X_p_hat), _ptr(replaced),
+                                           _ptr(n_replaced), _stream(stream)))
+
+
+def s3gs_scale_remedy(ctx, X_ak_hat, hw_ak, X_n, hw_n, matches, n_matches, sigma, n_used, stream=None):
+    check(ctx, lib().s3gs_scale_remedy(ctx, _ptr(X_ak_hat), int(hw_ak), _ptr(X_n), int(hw_n), _ptr(matches),
+                                       int(n_matches), _ptr(sigma), _ptr(n_used), _stream(stream)))
+
+
+def s3gs_pose_adam_default(**kw) -> PoseAdam:
+    p = PoseAdam()
+    lib().s3gs_pose_adam_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def s3gs_se3_exp(ctx, n, tau, E, stream=None):
+    check(ctx, lib().s3gs_se3_exp(ctx, int(n), _ptr(tau), _ptr(E), _stream(stream)))
+
+
+def s3gs_pose_update(ctx, n_views, d_twist, hp, adam_m, adam_v, step, T_cw, delta=None, frozen=None, stream=None):
+    check(ctx, lib().s3gs_pose_update(ctx, int(n_views), _ptr(d_twist), ctypes.byref(hp), _ptr(adam_m), _ptr(adam_v),
+                                      _ptr(step), _ptr(T_cw), _ptr(delta), _ptr(frozen), _stream(stream)))

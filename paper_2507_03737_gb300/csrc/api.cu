@@ -111,6 +111,14 @@ s3gs_status cuda_fail(s3gs_ctx *ctx, cudaError_t e, const char *where) {
 
 }  // namespace
 
+namespace s3gs {
+s3gs_status ctx_error(s3gs_ctx *ctx, s3gs_status st, const char *msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+int ctx_device(const s3gs_ctx *ctx) { return ctx ? ctx->device : 0; }
+}  // namespace s3gs
+
 bool capturing(cudaStream_t s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {

@@ -285,4 +285,9 @@ struct LossArgs {
 int loss_blocks_per_view();
 cudaError_t launch_loss(const LossArgs &a, const ViewBatch &vb, cudaStream_t s);
 
+// Context access for entry points defined outside api.cu: record an error
+// message on the context and return the status; the context's device.
+s3gs_status ctx_error(s3gs_ctx *ctx, s3gs_status st, const char *msg);
+int ctx_device(const s3gs_ctx *ctx);
+
 }  // namespace s3gs

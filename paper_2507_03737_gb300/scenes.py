@@ -255,3 +255,49 @@ def perturb_scene(sc: Scene, seed: int, sigma_pos=0.02, sigma_col=0.05) -> Scene
     out.means = (sc.means + rng.normal(0, sigma_pos, sc.means.shape)).astype(np.float32)
     out.colors = (sc.colors + rng.normal(0, sigma_col, sc.colors.shape)).astype(np.float32)
     return out
+
+
+def pointmap_pair(width: int, height: int, seed: int, scale: float = 1.1, fx: float = 718.0, fy: float = 718.0,
+                  hole_frac: float = 0.05, bad_frac: float = 0.15, noise: float = 0.02):
+    """A seeded (rendered, pre-trained) pair of camera-frame pointmaps, float32 (3, H, W).
+
+    Stands in for the 3DGS pointmap X^r and a learned pointmap prior X^p of a
+    driving frame (Sec. 3.3): a ground plane 1.65 m below the camera, a far
+    background at 60-80 m and a dozen box obstacles at 5-40 m, seen through a
+    pinhole camera. X^p is the same geometry at 1/scale of the scene's size with
+    per-pixel multiplicative depth noise and, over ``bad_frac`` of the image in
+    random blocks, depths distorted by a factor in [0.5, 2] (poorly predicted
+    regions). X^r has holes (all-zero points, as where a render has no
+    Gaussians) over ``hole_frac`` of the image in random blocks.
+    """
+    rng = np.random.default_rng(seed)
+    cx, cy = width / 2.0 - 0.5, height / 2.0 - 0.5
+    jj, ii = np.meshgrid(np.arange(height, dtype=np.float64), np.arange(width, dtype=np.float64), indexing="ij")
+    z = rng.uniform(60.0, 80.0) + rng.normal(0.0, 0.5, (height, width))
+    below = jj > cy + 1.0
+    ground = np.where(below, 1.65 * fy / np.maximum(jj - cy, 1e-6), np.inf)
+    z = np.where(below, np.minimum(z, np.clip(ground, 2.0, 80.0)), z)
+
+    def blocks(frac, lo, hi):
+        m = np.zeros((height, width), dtype=bool)
+        target = frac * width * height
+        while m.sum() < target:
+            bw = int(rng.integers(lo, hi + 1)); bh = int(rng.integers(lo, hi + 1))
+            x0 = int(rng.integers(0, max(width - bw, 0) + 1)); y0 = int(rng.integers(0, max(height - bh, 0) + 1))
+            m[y0:y0 + bh, x0:x0 + bw] = True
+        return m
+
+    for _ in range(12):
+        bw = int(rng.integers(max(width // 40, 2), max(width // 8, 3)))
+        bh = int(rng.integers(max(height // 20, 2), max(height // 3, 3)))
+        x0 = int(rng.integers(0, max(width - bw, 0) + 1)); y0 = int(rng.integers(0, max(height - bh, 0) + 1))
+        z[y0:y0 + bh, x0:x0 + bw] = np.minimum(z[y0:y0 + bh, x0:x0 + bw], rng.uniform(5.0, 40.0))
+    ray = np.stack([(ii - cx) / fx, (jj - cy) / fy, np.ones_like(ii)])
+    X_true = ray * z[None]
+    X_r = X_true * (1.0 + rng.normal(0.0, 0.5 * noise, (1, height, width)))
+    X_r[:, blocks(hole_frac, 4, max(min(width, height) // 6, 5))] = 0.0
+    depth_factor = 1.0 + rng.normal(0.0, noise, (height, width))
+    bad = blocks(bad_frac, 6, max(min(width, height) // 4, 7))
+    depth_factor[bad] *= rng.uniform(0.5, 2.0, int(bad.sum()))
+    X_p = X_true / scale * depth_factor[None]
+    return X_r.astype(np.float32), X_p.astype(np.float32)

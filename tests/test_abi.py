@@ -9,13 +9,15 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "s3gs.h")
+INCLUDE = os.path.join(ROOT, "include")
+HEADERS = sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(s3gs_[a-z_0-9]+)\s*\(", text)
+    names = []
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names += re.findall(r"\b(s3gs_[a-z_0-9]+)\s*\(", text)
     return sorted(set(names))
 
 
@@ -30,7 +32,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("s3gs_create", "s3gs_destroy", "s3gs_render_fwd", "s3gs_render_bwd", "s3gs_reserve",
-                 "s3gs_state_create", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_last_error"):
+                 "s3gs_state_create", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_last_error",
+                 "s3gs_scale_align", "s3gs_pointmap_replace", "s3gs_scale_remedy"):
         assert must in names
 
 
@@ -66,3 +69,18 @@ def test_no_cpu_fallback_in_product_package():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "s3gs_oracle" not in src, f
+
+
+def test_align_params_and_workspace_are_host_only(lib):
+    from paper_2507_03737_gb300 import binding as B
+    assert ctypes.sizeof(B.AlignParams) == 4 * 6
+    p = B.s3gs_align_params_default()
+    assert (p.patch, p.max_iter) == (10, 3)
+    assert abs(p.delta_mu - 0.3) < 1e-7 and abs(p.delta_sigma - 0.3) < 1e-7
+    assert abs(p.eps_r - 0.1) < 1e-7 and abs(p.tau - 0.01) < 1e-9
+    wh, nv = B.view_sizes([(1241, 376), (23, 7)])
+    # 1241x376 at P = 10: 38 patch rows x ceil(125 / 25) CTAs; 23x7: 1 x 1; 16 bytes per CTA
+    assert B.s3gs_scale_align_workspace(wh, nv, 10) == 16 * (38 * 5 + 1)
+    for bad in (0, 33):
+        with pytest.raises(B.S3GSError):
+            B.s3gs_scale_align_workspace(wh, nv, bad)

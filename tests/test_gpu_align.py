@@ -1,0 +1,246 @@
+"""Parity of the CUDA scale alignment (Algorithm 1), pointmap replacement (Eq. 14)
+and remedial factor against the FP64 oracle, on seeded synthetic pointmaps.
+
+Tolerances (derived from the FP32 arithmetic of the kernels):
+  * scale factor: 2e-5 relative. The kernel sums each CTA's correct points in
+    FP32 (at most 3 P rows per thread, then a 5-level warp tree and 8 warps:
+    about 46 roundings of 2^-24 in the worst case for each sum) and the CTAs
+    in double, so each sum is within ~3e-6 relative and their ratio within ~6e-6.
+  * decisions (candidate patches, correct points, replaced points) are FP32 on
+    the GPU and FP64 in the oracle; they are compared exactly on every point
+    whose oracle decision is at least 1e-4 (relative) from its threshold, and
+    the cases below are chosen so that every patch decision of every iteration
+    is at least that far from its threshold.
+"""
+import numpy as np
+import pytest
+
+from oracle import align_oracle as A
+from paper_2507_03737_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+SCALE_TOL = 2e-5
+MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module")
+def AL():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2507_03737_gb300.slam import Aligner
+    a = Aligner(device=0)
+    yield a
+    a.close()
+
+
+def _pack(pairs):
+    import torch
+    Xr = np.concatenate([p[0].reshape(-1) for p in pairs])
+    Xp = np.concatenate([p[1].reshape(-1) for p in pairs])
+    return torch.from_numpy(Xr).cuda(), torch.from_numpy(Xp).cuda()
+
+
+def _views(sizes):
+    return [(w, h) for (w, h) in sizes]
+
+
+def _check_view(ref, sigma, n_cp, insufficient, cp_mask):
+    assert min(m[0] for m in ref["min_margins"]) > MARGIN, "case has a patch decision within the margin"
+    assert abs(sigma - ref["sigma"]) <= SCALE_TOL * abs(ref["sigma"]), (sigma, ref["sigma"])
+    clear = ref["point_margin"] > MARGIN
+    np.testing.assert_array_equal(cp_mask[clear], ref["cp"][clear])
+    assert abs(n_cp - ref["n_cp"]) <= int((~clear).sum())
+    assert bool(insufficient) == ref["insufficient"]
+
+
+# (size, scale of the prior, seed); seeds are the first from 11 up whose patch
+# decisions stay clear of the margin at P = 8, 10, 16 and 32 in every iteration.
+CASES = [((160, 120), 1.1, 11), ((97, 53), 0.85, 11), ((1241, 376), 1.2, 12), ((1241, 376), 1.5, 12),
+         ((33, 17), 1.05, 11), ((640, 480), 0.9, 11)]
+# seeds from 100 up with clear patch decisions at the twelve scales of the window test
+WINDOW_SEEDS = [101, 103, 104, 105, 106, 107, 109, 110, 111, 112, 114, 119]
+
+
+@pytest.mark.parametrize("patch", [10, 8, 16, 32])
+def test_batched_alignment_matches_oracle(AL, patch):
+    from paper_2507_03737_gb300 import binding as B
+    sizes = [c[0] for c in CASES]
+    pairs = [scenes.pointmap_pair(w, h, seed=sd, scale=s) for (w, h), s, sd in CASES]
+    Xr, Xp = _pack(pairs)
+    params = B.s3gs_align_params_default(patch=patch)
+    out = AL.align(Xr, Xp, _views(sizes), params, want_mask=True)
+    sig = out["sigma"].cpu().numpy(); ncp = out["n_cp"].cpu().numpy()
+    ins = out["insufficient"].cpu().numpy(); mask = out["cp_mask"].cpu().numpy().astype(bool)
+    off = 0
+    for v, ((w, h), _, _) in enumerate(CASES):
+        ref = A.align(pairs[v][0], pairs[v][1], P=patch)
+        _check_view(ref, float(sig[v]), int(ncp[v]), int(ins[v]), mask[off:off + w * h].reshape(h, w))
+        off += w * h
+
+
+@pytest.mark.parametrize("max_iter,init", [(1, None), (5, None), (2, 1.3)])
+def test_iterations_and_initial_factor(AL, max_iter, init):
+    import torch
+    from paper_2507_03737_gb300 import binding as B
+    Xr_np, Xp_np = scenes.pointmap_pair(300, 200, seed=22, scale=1.4)  # first seed from 21 with clear decisions
+    Xr, Xp = _pack([(Xr_np, Xp_np)])
+    params = B.s3gs_align_params_default(max_iter=max_iter)
+    s0 = None if init is None else torch.tensor([init], dtype=torch.float32, device="cuda")
+    out = AL.align(Xr, Xp, [(300, 200)], params, sigma_init=s0, want_mask=True)
+    ref = A.align(Xr_np, Xp_np, max_iter=max_iter,
+                  sigma_init=1.0 if init is None else float(np.float32(init)))
+    _check_view(ref, float(out["sigma"][0]), int(out["n_cp"][0]), int(out["insufficient"][0]),
+                out["cp_mask"].cpu().numpy().astype(bool).reshape(200, 300))
+
+
+def test_no_candidates_keeps_the_factor_and_flags_the_view(AL):
+    rng = np.random.default_rng(31)
+    Xr_np = np.stack([rng.uniform(-5, 5, (40, 50)), rng.uniform(-1, 1, (40, 50)), rng.uniform(5, 50, (40, 50))])
+    Xp_np = Xr_np / 3.0                   # outside the 30 % gate everywhere
+    Xr, Xp = _pack([(Xr_np.astype(np.float32), Xp_np.astype(np.float32))])
+    out = AL.align(Xr, Xp, [(50, 40)], want_mask=True)
+    assert float(out["sigma"][0]) == 1.0 and int(out["n_cp"][0]) == 0
+    assert int(out["insufficient"][0]) == 1 and int(out["cp_mask"].sum()) == 0
+
+
+def test_exact_rescaling_recovers_scale_on_gpu(AL):
+    rng = np.random.default_rng(32)
+    z = rng.uniform(5, 50, (64, 90))
+    Xr_np = np.stack([rng.uniform(-0.5, 0.5, z.shape) * z, rng.uniform(-0.2, 0.2, z.shape) * z, z]).astype(np.float32)
+    Xp_np = (Xr_np / np.float32(1.25)).astype(np.float32)
+    Xr, Xp = _pack([(Xr_np, Xp_np)])
+    out = AL.align(Xr, Xp, [(90, 64)])
+    ref = A.align(Xr_np, Xp_np)
+    assert abs(float(out["sigma"][0]) - ref["sigma"]) <= SCALE_TOL * ref["sigma"]
+    assert int(out["n_cp"][0]) == ref["n_cp"] == 64 * 90
+
+
+def test_replacement_matches_oracle_with_a_given_factor(AL):
+    import torch
+    sizes = [(160, 120), (1241, 376), (13, 7)]
+    pairs = [scenes.pointmap_pair(w, h, seed=40 + i, scale=1.15) for i, (w, h) in enumerate(sizes)]
+    Xr, Xp = _pack(pairs)
+    sig = np.array([1.15, 1.1, 1.3], dtype=np.float32)
+    out = AL.replace(Xr, Xp, torch.from_numpy(sig).cuda(), sizes)
+    got_r = out["X_r_hat"].cpu().numpy(); got_p = out["X_p_hat"].cpu().numpy()
+    rep = out["replaced"].cpu().numpy().astype(bool); nrep = out["n_replaced"].cpu().numpy()
+    off = 0
+    for v, (w, h) in enumerate(sizes):
+        ref_r, ref_p, ref_rep, margin = A.replace(pairs[v][0], pairs[v][1], float(sig[v]))
+        sl3 = slice(3 * off, 3 * (off + w * h)); sl = slice(off, off + w * h)
+        clear = margin.reshape(-1) > MARGIN
+        np.testing.assert_array_equal(rep[sl][clear], ref_rep.reshape(-1)[clear])
+        assert abs(int(nrep[v]) - int(ref_rep.sum())) <= int((~clear).sum())
+        assert int(nrep[v]) == int(rep[sl].sum())
+        np.testing.assert_allclose(got_p[sl3], ref_p.reshape(-1), rtol=1e-6, atol=0)
+        # every output point is the rendered point or the aligned prior point, as its flag says
+        r3 = got_r[sl3].reshape(3, -1); xr = pairs[v][0].reshape(3, -1); xp = got_p[sl3].reshape(3, -1)
+        np.testing.assert_array_equal(r3[:, ~rep[sl]], xr[:, ~rep[sl]])
+        np.testing.assert_array_equal(r3[:, rep[sl]], xp[:, rep[sl]])
+        off += w * h
+
+
+def test_replacement_in_place_and_idempotent(AL):
+    import torch
+    Xr_np, Xp_np = scenes.pointmap_pair(200, 100, seed=50, scale=1.0)
+    Xr, Xp = _pack([(Xr_np, Xp_np)])
+    sigma = torch.ones(1, device="cuda")
+    first = AL.replace(Xr, Xp, sigma, [(200, 100)])
+    work = Xr.clone()
+    AL.replace(work, Xp, sigma, [(200, 100)], out=dict(X_r_hat=work, X_p_hat=None, replaced=None, n_replaced=None))
+    assert torch.equal(work, first["X_r_hat"])
+    again = AL.replace(work, Xp, sigma, [(200, 100)])
+    assert int(again["n_replaced"][0]) == 0 and torch.equal(again["X_r_hat"], work)
+
+
+def test_remedy_matches_oracle_and_skips_bad_indices(AL):
+    import torch
+    rng = np.random.default_rng(60)
+    Xak, _ = scenes.pointmap_pair(120, 80, seed=61, scale=1.0)
+    Xn, _ = scenes.pointmap_pair(100, 90, seed=62, scale=1.0)
+    m = np.stack([rng.integers(0, 120 * 80, 5000), rng.integers(0, 100 * 90, 5000)], axis=1)
+    bad = np.array([[-1, 3], [5, 100 * 90], [120 * 80, 0]])
+    matches = np.concatenate([m, bad]).astype(np.int32)
+    sigma, used = AL.remedy(torch.from_numpy(Xak).cuda(), torch.from_numpy(Xn).cuda(), torch.from_numpy(matches))
+    ref = A.remedy_scale(Xak, Xn, m)
+    assert abs(float(sigma[0]) - ref) <= 1e-6 * abs(ref)
+    assert int(used[0]) == 5000
+    sigma0, used0 = AL.remedy(torch.from_numpy(Xak).cuda(), torch.from_numpy(Xn).cuda(),
+                              torch.from_numpy(bad.astype(np.int32)))
+    assert float(sigma0[0]) == 1.0 and int(used0[0]) == 0
+
+
+def test_remedy_flow_recovers_an_out_of_gate_scale(AL):
+    """A view whose prior is 3x too small finds no candidates; the remedial
+    factor from matches with an aligned neighbour plus one iteration recovers it."""
+    import torch
+    rng = np.random.default_rng(70)
+    z = rng.uniform(5, 50, (50, 60))
+    Xr_np = np.stack([rng.uniform(-0.5, 0.5, z.shape) * z, rng.uniform(-0.2, 0.2, z.shape) * z, z]).astype(np.float32)
+    Xp_np = (Xr_np / np.float32(3.0)).astype(np.float32)
+    Xr, Xp = _pack([(Xr_np, Xp_np)])
+    # the adjacent keyframe's aligned map sees the same points (rows shifted by 5)
+    ak = np.zeros_like(Xr_np); ak[:, :45] = Xr_np[:, 5:]
+    idx_n = np.arange(5 * 60, 50 * 60); idx_ak = idx_n - 5 * 60
+    noisy = ak * (1.0 + rng.normal(0, 0.01, (1, 50, 60))).astype(np.float32)
+    matches = torch.from_numpy(np.stack([idx_ak, idx_n], axis=1).astype(np.int32))
+    res = AL.align_with_remedy(Xr, Xp, [(60, 50)], remedy={0: (torch.from_numpy(noisy).cuda(), matches)})
+    s_rem = A.remedy_scale(noisy, Xp_np, np.stack([idx_ak, idx_n], axis=1))
+    ref = A.align(Xr_np, Xp_np, max_iter=1, sigma_init=float(np.float32(s_rem)))
+    assert abs(float(res["sigma"][0]) - ref["sigma"]) <= SCALE_TOL * ref["sigma"]
+    assert abs(ref["sigma"] - 3.0) <= 1e-6 * 3.0
+    assert int(res["insufficient"][0]) == 0
+
+
+def test_full_window_batched(AL):
+    """Twelve 1241x376 views in one call (the launch configuration bench.py times)."""
+    sizes = [(1241, 376)] * 12
+    scales = np.linspace(0.8, 1.45, 12)
+    pairs = [scenes.pointmap_pair(w, h, seed=WINDOW_SEEDS[i], scale=float(scales[i])) for i, (w, h) in enumerate(sizes)]
+    Xr, Xp = _pack(pairs)
+    out = AL.align(Xr, Xp, sizes, want_mask=True)
+    sig = out["sigma"].cpu().numpy(); ncp = out["n_cp"].cpu().numpy()
+    ins = out["insufficient"].cpu().numpy(); mask = out["cp_mask"].cpu().numpy().astype(bool)
+    for v in range(12):
+        ref = A.align(*pairs[v])
+        _check_view(ref, float(sig[v]), int(ncp[v]), int(ins[v]), mask[v * 466616:(v + 1) * 466616].reshape(376, 1241))
+
+
+def test_graph_capture_matches_eager(AL):
+    import torch
+    sizes = [(320, 200), (160, 120)]
+    pairs = [scenes.pointmap_pair(w, h, seed=80 + i, scale=1.1) for i, (w, h) in enumerate(sizes)]
+    Xr, Xp = _pack(pairs)
+    eager = AL.align(Xr, Xp, sizes, want_mask=True)
+    eager_rep = AL.replace(Xr, Xp, eager["sigma"], sizes)
+    torch.cuda.synchronize()
+    out = {k: (torch.empty_like(v) if v is not None else None) for k, v in eager.items()}
+    rep = {k: (torch.empty_like(v) if v is not None else None) for k, v in eager_rep.items()}
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        AL.align(Xr, Xp, sizes, out=out)
+        AL.replace(Xr, Xp, out["sigma"], sizes, out=rep)
+    g.replay()
+    torch.cuda.synchronize()
+    for k in eager:
+        assert torch.equal(out[k], eager[k]), k
+    for k in eager_rep:
+        assert torch.equal(rep[k], eager_rep[k]), k
+
+
+def test_argument_errors(AL):
+    import torch
+    from paper_2507_03737_gb300 import binding as B
+    Xr, Xp = _pack([scenes.pointmap_pair(20, 10, seed=90)])
+    for bad in (dict(patch=0), dict(patch=33), dict(max_iter=0), dict(eps_r=-1.0), dict(delta_mu=float("nan"))):
+        with pytest.raises(B.S3GSError):
+            AL.align(Xr, Xp, [(20, 10)], B.s3gs_align_params_default(**bad))
+    wh, nv = B.view_sizes([(20, 10)])
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    sig = torch.empty(1, device="cuda")
+    with pytest.raises(B.S3GSError):
+        B.s3gs_scale_align(AL.ctx, wh, nv, Xr, Xp, B.s3gs_align_params_default(), None, sig, None, None, None, small)
+    with pytest.raises(B.S3GSError):
+        AL.replace(Xr, Xp, sig, [(20, 10)], eps_m=-0.1)
