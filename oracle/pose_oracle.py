@@ -79,8 +79,8 @@ def refine(scene, cameras, target_rgb, iters, lr_rho=1e-3, lr_phi=1e-3, weight=N
            eps=1e-8, near_z=0.2):
     """Pose refinement of every view (independently) for ``iters`` iterations.
     target_rgb: packed planar rgb of all views; weight: packed per-pixel weights
-    (None = 1). Returns the list of 3x4 poses after each iteration (per view)
-    and the loss before each iteration."""
+    (None = 1). Returns the list of 3x4 poses after each iteration (per view),
+    the loss before each iteration and the twist gradients of each iteration."""
     cams = [dict(c, T_cw=np.asarray(c["T_cw"], dtype=np.float64).reshape(3, 4)) for c in cameras]
     V = len(cams)
     P = sum(c["width"] * c["height"] for c in cams)
@@ -88,7 +88,7 @@ def refine(scene, cameras, target_rgb, iters, lr_rho=1e-3, lr_phi=1e-3, weight=N
     w = np.ones(P) if weight is None else np.asarray(weight, dtype=np.float64)
     lr = np.array([lr_rho] * 3 + [lr_phi] * 3)
     m = np.zeros((V, 6)); v = np.zeros((V, 6))
-    poses, losses = [], []
+    poses, losses, grads = [], [], []
     for it in range(1, iters + 1):
         out = O.render_fwd(scene, cameras=cams, near_z=near_z)
         r = out["rgb"] - t_rgb
@@ -98,10 +98,11 @@ def refine(scene, cameras, target_rgb, iters, lr_rho=1e-3, lr_phi=1e-3, weight=N
         losses.append(float((w3 * np.abs(r)).sum() / (3.0 * P)))
         d_rgb = w3 * np.sign(r) / (3.0 * P)
         g = O.render_bwd(scene, d_rgb=d_rgb, cameras=cams, near_z=near_z)["twist"]
+        grads.append(g.copy())
         step = []
         for k in range(V):
             delta, m[k], v[k] = adam_step(g[k], m[k], v[k], it, lr, beta1, beta2, eps)
             cams[k] = dict(cams[k], T_cw=apply_left(se3_exp(delta), cams[k]["T_cw"]))
             step.append(cams[k]["T_cw"].copy())
         poses.append(step)
-    return poses, losses
+    return poses, losses, grads

@@ -66,7 +66,7 @@ def _scene_and_target():
 
 def test_refine_fixed_point_at_the_true_pose():
     sc, tgt = _scene_and_target()
-    poses, losses = PO.refine(sc, sc.cameras, tgt, iters=3)
+    poses, losses, _ = PO.refine(sc, sc.cameras, tgt, iters=3)
     T0 = np.asarray(sc.cameras[0]["T_cw"], np.float64)
     for step in poses:
         np.testing.assert_array_equal(step[0], T0)
@@ -78,7 +78,7 @@ def test_refine_descends_from_a_perturbed_pose():
     T0 = np.asarray(sc.cameras[0]["T_cw"], np.float64)
     start = PO.apply_left(PO.se3_exp([0.02, -0.015, 0.01, 0.01, -0.008, 0.006]), T0)
     cams = [dict(sc.cameras[0], T_cw=start)]
-    poses, losses = PO.refine(sc, cams, tgt, iters=30, lr_rho=2e-3, lr_phi=2e-3)
+    poses, losses, _ = PO.refine(sc, cams, tgt, iters=30, lr_rho=2e-3, lr_phi=2e-3)
     err0 = np.linalg.norm(start - T0)
     err = np.linalg.norm(poses[-1][0] - T0)
     assert losses[-1] < 0.5 * losses[0]
