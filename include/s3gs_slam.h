@@ -3,8 +3,9 @@
  * outputs on the GPU: patch-based pointmap scale alignment (Sec. 3.3.1 and
  * Algorithm 1 of the supplementary material), pointmap replacement (Sec.
  * 3.3.2, Eq. 14), the remedial scale factor (supplementary material, the
- * paragraph after Algorithm 1) and the pose update of photometric tracking
- * (Sec. 3.2.2, Eq. 10/11).
+ * paragraph after Algorithm 1), the pose update of photometric tracking
+ * (Sec. 3.2.2, Eq. 10/11), the map optimiser step (Eq. 16/17) and keyframe
+ * covisibility / window management (supplementary material, Eq. S1/S2).
  *
  * Conventions are those of s3gs.h: float32 device tensors, packed views
  * (pointmaps planar [3][H][W] per view, view v starting at 3 P_v with
@@ -143,6 +144,97 @@ s3gs_status s3gs_se3_exp(s3gs_ctx *ctx, int64_t n, const float *tau, float *E, v
 s3gs_status s3gs_pose_update(s3gs_ctx *ctx, int32_t n_views, const float *d_twist, const s3gs_pose_adam *hp,
                              float *adam_m, float *adam_v, int32_t *step, float *T_cw, float *delta,
                              const uint8_t *frozen, void *stream);
+
+/* ---- Map optimiser step (Eq. 17) with the isotropic regulariser (Eq. 16) ----
+ * Readings: s_i = exp(log_scale_i) and s~_i = mean of its three entries;
+ * L_iso = lambda_iso * sum_i ||s_i - s~_i 1||_1 summed over Gaussians as
+ * printed (scale lambda_iso by 1 / (3 |G|) for a mean), with d|x|/dx = sign(x)
+ * (0 at 0). The optimiser is Adam (the paper names none) with one step count,
+ * a learning rate per tensor and a separate one for the SH bands l >= 1; the
+ * default rates are this library's choice. The window poses take the same
+ * kind of step through s3gs_pose_update. */
+typedef struct {
+    float lr_means;        /* default 1.6e-4 */
+    float lr_log_scales;   /* default 5e-3 */
+    float lr_quats;        /* default 1e-3 */
+    float lr_opacity;      /* default 5e-2 */
+    float lr_colors;       /* colour / SH band 0, default 2.5e-3 */
+    float lr_colors_rest;  /* SH bands l >= 1, default 1.25e-4 */
+    float beta1;           /* default 0.9 */
+    float beta2;           /* default 0.999 */
+    float eps;             /* default 1e-15 */
+    float lambda_iso;      /* default 10 (supplementary material) */
+} s3gs_map_adam;
+
+/* Host only: fills the defaults above. */
+void s3gs_map_adam_default(s3gs_map_adam *hp);
+
+/* One fused Adam step over all Gaussian tensors, in place, in one launch plus
+ * a one-thread counter update. params / grads / adam_m / adam_v are HOST
+ * arrays of 5 DEVICE pointers in the order means [n][3], log_scales [n][3],
+ * quats [n][4], opacity_logits [n], colors [n][(d+1)^2][3] (the layouts of
+ * s3gs_gaussians); a NULL gradient pointer means a zero gradient for that
+ * tensor (momentum still moves it, as in Adam); moments start at zero. step
+ * is a device int32 counter (0 before the first step), advanced by one.
+ * Returns S3GS_E_INVALID for NULL arrays or pointers, n < 0, sh_degree outside
+ * 0..3 or hyperparameters out of range. */
+s3gs_status s3gs_map_adam_step(s3gs_ctx *ctx, int64_t n, int32_t sh_degree, float *const params[5],
+                               const float *const grads[5], float *const adam_m[5], float *const adam_v[5],
+                               int32_t *step, const s3gs_map_adam *hp, void *stream);
+
+/* ---- Keyframe covisibility and window management (supplementary material,
+ * "Keyframe Management", Eq. S1/S2) ----
+ * Readings: the visible set G_i^v of view i is the set of Gaussians the last
+ * forward projected into view i with a non-empty pixel footprint (near plane,
+ * guard cone and 3-sigma tile cover of s3gs.h); IOU and OC are 0 when their
+ * denominator is 0; the median depth is the lower median (rank
+ * floor((N - 1) / 2)) of the N pixels with depth > 0, 0 if there are none. */
+
+/* Intersection counts of the visible sets of the last forward on `state`:
+ * counts device int64 [V][V] out (counts[i][i] = |G_i|), iou and oc device
+ * float [V][V] out (optional), V = that forward's n_views. Enqueued on
+ * `stream`, which the caller orders after the forward. Returns S3GS_E_STATE
+ * if the state has no forward. */
+s3gs_status s3gs_covisibility(s3gs_ctx *ctx, s3gs_state *state, int64_t *counts, float *iou, float *oc,
+                              void *stream);
+
+/* Host only: workspace bytes of s3gs_median_depth for n_views views. */
+s3gs_status s3gs_median_depth_workspace(int32_t n_views, size_t *bytes);
+
+/* Median depth per view of packed depth maps (view_wh host [n_views][2]):
+ * median device float [n_views] out, n_valid device int64 [n_views] out
+ * (optional, the number of positive depths); workspace device, 16-byte
+ * aligned. Exact (a radix select on the float bits, no rounding). */
+s3gs_status s3gs_median_depth(s3gs_ctx *ctx, const int32_t *view_wh, int32_t n_views, const float *depth,
+                              float *median, int64_t *n_valid, void *workspace, size_t workspace_bytes,
+                              void *stream);
+
+/* Window parameters (the supplementary material's values as defaults:
+ * k_I = 0.9, k_d = 0.08, k_o = 0.3, |W| = 8). */
+typedef struct {
+    float k_iou;         /* a frame with IOU < k_iou against the latest keyframe becomes a keyframe */
+    float k_d;           /* ... as does one that moved more than k_d times its median depth */
+    float k_oc;          /* window keyframes with OC < k_oc against a new keyframe leave */
+    int32_t max_window;  /* window size, the new keyframe included */
+} s3gs_keyframe_params;
+
+/* Host only: fills the defaults above. */
+void s3gs_keyframe_params_default(s3gs_keyframe_params *p);
+
+/* Host only: 1 if frame i becomes a keyframe given IOU(i, j) with the latest
+ * keyframe j, the translation distance d_ij and i's median depth, else 0;
+ * -1 if p is NULL. */
+int32_t s3gs_keyframe_is_new(const s3gs_keyframe_params *p, float iou_ij, float d_ij, float median_depth_i);
+
+/* Host only: the window after keyframe new_id joined. window_ids [n] are the
+ * current keyframes (oldest first) and oc_with_new [n] their OC with the new
+ * keyframe. Every keyframe with OC < k_oc leaves; while the window would
+ * exceed max_window, the remaining one with the lowest OC leaves (the earlier
+ * one on ties); new_id is appended. out_ids (capacity n + 1) and *out_n
+ * receive the result. */
+s3gs_status s3gs_keyframe_window_update(const s3gs_keyframe_params *p, const int32_t *window_ids,
+                                        const float *oc_with_new, int32_t n, int32_t new_id, int32_t *out_ids,
+                                        int32_t *out_n);
 
 #ifdef __cplusplus
 }

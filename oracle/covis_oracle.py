@@ -33,8 +33,10 @@ DEFAULTS = dict(k_iou=0.9, k_d=0.08, k_oc=0.3, max_window=8)
 
 
 def projected_sets(scene, cameras, near_z=0.2):
-    """Boolean [V][n] visibility from the FP64 projection, and the distance (in
-    pixels) of each footprint's edge from the image border (small = ambiguous)."""
+    """Boolean [V][n] visibility from the FP64 projection (guard slope 1.5), and
+    the distance (in pixels) of each footprint's edge from the image border
+    (0 where the near-plane or guard decision itself is within 1e-5 of its
+    threshold; small = ambiguous)."""
     V, n = len(cameras), scene.n
     vis = np.zeros((V, n), dtype=bool)
     slack = np.full((V, n), np.inf)
@@ -49,6 +51,15 @@ def projected_sets(scene, cameras, near_z=0.2):
         gy = np.minimum(p["v"] + ry, (H - 1) - (p["v"] - ry))
         vis[v] = ok & (gx >= 0) & (gy >= 0)
         slack[v] = np.where(ok, np.minimum(np.abs(gx), np.abs(gy)), np.inf)
+        # near-plane and guard-cone decisions within 1e-5 of their threshold are
+        # ambiguous in FP32 as well
+        T = np.asarray(cam["T_cw"], dtype=np.float64).reshape(3, 4)
+        pc = np.asarray(scene.means, dtype=np.float64) @ T[:, :3].T + T[:, 3]
+        z = pc[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            m = np.minimum(np.abs(z - near_z) / near_z,
+                           np.minimum(np.abs(np.abs(pc[:, 0] / z) - 1.5), np.abs(np.abs(pc[:, 1] / z) - 1.5)) / 1.5)
+        slack[v] = np.where((z > 0) & (m < 1e-5), 0.0, slack[v])
     return vis, slack
 
 

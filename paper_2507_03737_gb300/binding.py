@@ -24,7 +24,10 @@ __all__ = [
     "s3gs_set_timing", "s3gs_read_timing", "STAGES", "s3gs_mapping_loss_noalloc",
     "make_cameras", "make_gaussians", "check", "AlignParams", "s3gs_align_params_default",
     "s3gs_scale_align_workspace", "s3gs_scale_align", "s3gs_pointmap_replace", "s3gs_scale_remedy", "view_sizes",
-    "PoseAdam", "s3gs_pose_adam_default", "s3gs_se3_exp", "s3gs_pose_update",
+    "PoseAdam", "s3gs_pose_adam_default", "s3gs_se3_exp", "s3gs_pose_update", "KeyframeParams",
+    "s3gs_covisibility", "s3gs_median_depth_workspace", "s3gs_median_depth", "s3gs_keyframe_params_default",
+    "s3gs_keyframe_is_new", "s3gs_keyframe_window_update", "MapAdam", "s3gs_map_adam_default",
+    "s3gs_map_adam_step", "MAP_TENSORS",
 ]
 
 S3GS_OK, S3GS_E_INVALID, S3GS_E_CAPACITY, S3GS_E_CUDA = 0, -1, -2, -3
@@ -65,6 +68,16 @@ class Options(ctypes.Structure):
 class AlignParams(ctypes.Structure):
     _fields_ = [("patch", ctypes.c_int32), ("delta_mu", ctypes.c_float), ("delta_sigma", ctypes.c_float),
                 ("eps_r", ctypes.c_float), ("max_iter", ctypes.c_int32), ("tau", ctypes.c_float)]
+
+
+class KeyframeParams(ctypes.Structure):
+    _fields_ = [("k_iou", ctypes.c_float), ("k_d", ctypes.c_float), ("k_oc", ctypes.c_float),
+                ("max_window", ctypes.c_int32)]
+
+
+class MapAdam(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("lr_means", "lr_log_scales", "lr_quats", "lr_opacity", "lr_colors",
+                                              "lr_colors_rest", "beta1", "beta2", "eps", "lambda_iso")]
 
 
 class PoseAdam(ctypes.Structure):
@@ -121,6 +134,17 @@ def _load():
                                                  _P, _P]),
         "s3gs_scale_remedy": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64, _P,
                                              _P, _P]),
+        "s3gs_covisibility": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+        "s3gs_median_depth_workspace": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+        "s3gs_median_depth": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+        "s3gs_keyframe_params_default": (None, [ctypes.POINTER(KeyframeParams)]),
+        "s3gs_keyframe_is_new": (ctypes.c_int32, [ctypes.POINTER(KeyframeParams), ctypes.c_float, ctypes.c_float,
+                                                  ctypes.c_float]),
+        "s3gs_keyframe_window_update": (ctypes.c_int, [ctypes.POINTER(KeyframeParams), _P, _P, ctypes.c_int32,
+                                                       ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32)]),
+        "s3gs_map_adam_default": (None, [ctypes.POINTER(MapAdam)]),
+        "s3gs_map_adam_step": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, _P,
+                                              ctypes.POINTER(MapAdam), _P]),
         "s3gs_pose_adam_default": (None, [ctypes.POINTER(PoseAdam)]),
         "s3gs_se3_exp": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
         "s3gs_pose_update": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(PoseAdam), _P, _P, _P, _P, _P,
@@ -380,3 +404,68 @@ def s3gs_se3_exp(ctx, n, tau, E, stream=None):
 def s3gs_pose_update(ctx, n_views, d_twist, hp, adam_m, adam_v, step, T_cw, delta=None, frozen=None, stream=None):
     check(ctx, lib().s3gs_pose_update(ctx, int(n_views), _ptr(d_twist), ctypes.byref(hp), _ptr(adam_m), _ptr(adam_v),
                                       _ptr(step), _ptr(T_cw), _ptr(delta), _ptr(frozen), _stream(stream)))
+
+
+def s3gs_covisibility(ctx, state, counts, iou=None, oc=None, stream=None):
+    check(ctx, lib().s3gs_covisibility(ctx, state, _ptr(counts), _ptr(iou), _ptr(oc), _stream(stream)))
+
+
+def s3gs_median_depth_workspace(n_views) -> int:
+    b = ctypes.c_size_t()
+    st = lib().s3gs_median_depth_workspace(int(n_views), ctypes.byref(b))
+    if st != S3GS_OK:
+        raise S3GSError(st, "median_depth_workspace: n_views out of range")
+    return b.value
+
+
+def s3gs_median_depth(ctx, view_wh, n_views, depth, median, n_valid, workspace, stream=None):
+    ws = workspace.numel() * workspace.element_size()
+    check(ctx, lib().s3gs_median_depth(ctx, view_wh, int(n_views), _ptr(depth), _ptr(median), _ptr(n_valid),
+                                       workspace.data_ptr(), ws, _stream(stream)))
+
+
+def s3gs_keyframe_params_default(**kw) -> KeyframeParams:
+    p = KeyframeParams()
+    lib().s3gs_keyframe_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def s3gs_keyframe_is_new(params, iou_ij, d_ij, median_depth_i) -> bool:
+    r = lib().s3gs_keyframe_is_new(ctypes.byref(params), float(iou_ij), float(d_ij), float(median_depth_i))
+    if r < 0:
+        raise S3GSError(S3GS_E_INVALID, "keyframe_is_new: NULL parameters")
+    return bool(r)
+
+
+def s3gs_keyframe_window_update(params, window_ids, oc_with_new, new_id):
+    n = len(window_ids)
+    ids = (ctypes.c_int32 * max(n, 1))(*[int(x) for x in window_ids])
+    oc = (ctypes.c_float * max(n, 1))(*[float(x) for x in oc_with_new])
+    out = (ctypes.c_int32 * (n + 1))()
+    m = ctypes.c_int32()
+    st = lib().s3gs_keyframe_window_update(ctypes.byref(params), ids, oc, n, int(new_id), out, ctypes.byref(m))
+    if st != S3GS_OK:
+        raise S3GSError(st, "keyframe_window_update: bad arguments")
+    return [int(out[k]) for k in range(m.value)]
+
+
+MAP_TENSORS = ("means", "log_scales", "quats", "opacity_logits", "colors")
+
+
+def s3gs_map_adam_default(**kw) -> MapAdam:
+    p = MapAdam()
+    lib().s3gs_map_adam_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def s3gs_map_adam_step(ctx, params: dict, grads: dict, m: dict, v: dict, step, hp, stream=None):
+    """params / grads / m / v: dicts of CUDA tensors keyed by MAP_TENSORS (a missing
+    gradient is zero); params["sh_degree"] gives the colour layout."""
+    arr = lambda d, req: (_P * 5)(*[_ptr(d.get(k)) if not req else _ptr(d[k]) for k in MAP_TENSORS])
+    n = int(params["means"].shape[0])
+    check(ctx, lib().s3gs_map_adam_step(ctx, n, int(params["sh_degree"]), arr(params, True), arr(grads, False),
+                                        arr(m, True), arr(v, True), _ptr(step), ctypes.byref(hp), _stream(stream)))

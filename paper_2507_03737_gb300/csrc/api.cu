@@ -702,6 +702,18 @@ s3gs_status s3gs_debug_binning(s3gs_ctx *ctx, s3gs_state *st, uint64_t *keys, ui
     return S3GS_OK;
 }
 
+s3gs_status s3gs_covisibility(s3gs_ctx *ctx, s3gs_state *st, int64_t *counts, float *iou, float *oc,
+                              void *stream) {
+    if (!ctx) return S3GS_E_INVALID;
+    if (!st || !st->valid) return fail(ctx, S3GS_E_STATE, "covisibility: no forward on this state");
+    if (!counts) return fail(ctx, S3GS_E_INVALID, "covisibility: counts is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(launch_covis(st->vis_mask.p, st->g.n, st->vb.n_views, reinterpret_cast<unsigned long long *>(counts), iou, oc,
+                    ctx->num_sms, static_cast<cudaStream_t>(stream)),
+       "covisibility");
+    return S3GS_OK;
+}
+
 s3gs_status s3gs_set_counting(s3gs_ctx *ctx, int32_t enable) {
     if (!ctx) return S3GS_E_INVALID;
     ctx->counting = enable ? 1 : 0;

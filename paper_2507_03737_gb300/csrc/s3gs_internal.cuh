@@ -290,4 +290,9 @@ cudaError_t launch_loss(const LossArgs &a, const ViewBatch &vb, cudaStream_t s);
 s3gs_status ctx_error(s3gs_ctx *ctx, s3gs_status st, const char *msg);
 int ctx_device(const s3gs_ctx *ctx);
 
+// Pairwise visible-set intersection counts of V views from the per-Gaussian
+// view bitmask (counts [V][V], zeroed here), and IOU / OC when non-NULL.
+cudaError_t launch_covis(const unsigned *vis, long long n, int V, unsigned long long *counts, float *iou, float *oc,
+                         int num_sms, cudaStream_t s);
+
 }  // namespace s3gs

@@ -12,7 +12,7 @@ import torch
 
 from . import binding as B
 
-__all__ = ["Aligner", "PoseRefiner", "EPS_M"]
+__all__ = ["Aligner", "PoseRefiner", "MapOptimizer", "EPS_M"]
 
 EPS_M = 0.15  # Eq. 14 threshold used for all datasets (supplementary material)
 
@@ -198,3 +198,90 @@ class PoseRefiner:
 
     def poses(self):
         return self.T.view(self.V, 3, 4).cpu().numpy()
+
+
+class MapOptimizer:
+    """One mapping iteration of the keyframe window (Eq. 17), entirely on the
+    device: batched render of every window view, the mapping loss
+    alpha L_pho + (1 - alpha) L_geo (+ an optional depth term) against the
+    views' images and aligned pointmaps, the backward to all Gaussian
+    parameters and the window twists, the fused Adam step with L_iso (Eq. 16)
+    and the pose step with retraction. ``capture()`` records ``iters``
+    iterations into one CUDA graph."""
+
+    def __init__(self, renderer, params: dict, cameras, t_rgb, t_pointmap=None, t_depth=None, alpha=0.98,
+                 w_depth=0.0, hp: B.MapAdam | None = None, pose_hp: B.PoseAdam | None = None, frozen=None,
+                 iters: int = 1, options: B.Options | None = None):
+        import numpy as np
+        self.R = renderer
+        self.p = params
+        self.cameras = [dict(c) for c in cameras]
+        self.V = len(cameras)
+        dev = renderer.device
+        self.hp = hp if hp is not None else B.s3gs_map_adam_default()
+        self.pose_hp = pose_hp if pose_hp is not None else B.s3gs_pose_adam_default()
+        self.iters = int(iters)
+        self.options = B.Options.from_buffer_copy(options if options is not None else renderer.options)
+        self.alpha, self.w_depth = float(alpha), float(w_depth)
+        self.t_rgb, self.t_pm, self.t_depth = t_rgb, t_pointmap, t_depth
+        T0 = np.stack([np.asarray(c["T_cw"], np.float32).reshape(12) for c in cameras])
+        self.T = torch.from_numpy(T0).to(dev)
+        self.frozen = frozen
+        self.m = {k: torch.zeros_like(params[k]) for k in B.MAP_TENSORS}
+        self.v = {k: torch.zeros_like(params[k]) for k in B.MAP_TENSORS}
+        self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.pm_ = torch.zeros((self.V, 6), device=dev)
+        self.pv_ = torch.zeros((self.V, 6), device=dev)
+        self.pstep = torch.zeros(self.V, dtype=torch.int32, device=dev)
+        self.out = renderer.empty_outputs(cameras)
+        self.dout = {k: torch.zeros_like(v) for k, v in self.out.items() if k != "alpha"}
+        self.grads = {k: torch.zeros_like(params[k]) for k in B.MAP_TENSORS}
+        self.d_twist = torch.zeros((self.V, 6), device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.cam_arr = B.make_cameras(self.cameras)
+        self.graph = None
+
+    def iteration(self):
+        R, p, g = self.R, self.p, self.grads
+        gs = B.make_gaussians(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["colors"],
+                              p["sh_degree"])
+        B.s3gs_render_fwd(R.ctx, R.state, gs, self.cam_arr, self.V, self.T, self.options, self.out["rgb"],
+                          self.out["depth"], self.out["pointmap"], None)
+        B.s3gs_mapping_loss(R.ctx, self.cam_arr, self.V, self.out["rgb"], self.out["depth"], self.out["pointmap"],
+                            self.t_rgb, self.t_depth, self.t_pm, None, self.alpha,
+                            self.w_depth if self.t_depth is not None else 0.0,
+                            (1.0 - self.alpha) if self.t_pm is not None else 0.0,
+                            self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], self.loss)
+        B.s3gs_render_bwd(R.ctx, R.state, self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], None,
+                          g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["colors"], self.d_twist, 0)
+        B.s3gs_map_adam_step(R.ctx, p, g, self.m, self.v, self.step, self.hp)
+        B.s3gs_pose_update(R.ctx, self.V, self.d_twist, self.pose_hp, self.pm_, self.pv_, self.pstep, self.T,
+                           None, self.frozen)
+
+    def capture(self, headroom: float = 1.5):
+        """Size the state with one eager iteration, then record ``iters`` iterations.
+        The eager iteration is a real step; call it part of the optimisation."""
+        self.iteration()
+        torch.cuda.synchronize(self.R.device)
+        _, K, _ = B.s3gs_state_check(self.R.ctx, self.R.state)
+        P = sum(c["width"] * c["height"] for c in self.cameras)
+        tiles = sum(((c["width"] + 7) // 8) * ((c["height"] + 7) // 8) for c in self.cameras)
+        B.s3gs_reserve(self.R.ctx, self.R.state, int(self.p["means"].shape[0]), self.V, P, tiles,
+                       int(K * headroom) + 4096)
+        self.options.auto_grow = 0
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=self.R.device)
+        side.wait_stream(torch.cuda.current_stream(self.R.device))
+        with torch.cuda.graph(self.graph, stream=side):
+            for _ in range(self.iters):
+                self.iteration()
+        torch.cuda.synchronize(self.R.device)
+        return self.graph
+
+    def run(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def check(self):
+        B.s3gs_state_check(self.R.ctx, self.R.state)

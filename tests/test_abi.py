@@ -84,3 +84,27 @@ def test_align_params_and_workspace_are_host_only(lib):
     for bad in (0, 33):
         with pytest.raises(B.S3GSError):
             B.s3gs_scale_align_workspace(wh, nv, bad)
+
+
+def test_keyframe_window_logic_matches_oracle(lib):
+    """Host-only keyframe rules of the library against the oracle's reading."""
+    import numpy as np
+    from oracle import covis_oracle as C
+    from paper_2507_03737_gb300 import binding as B
+    p = B.s3gs_keyframe_params_default()
+    assert (abs(p.k_iou - 0.9) < 1e-7, abs(p.k_d - 0.08) < 1e-7, abs(p.k_oc - 0.3) < 1e-7, p.max_window) == \
+        (True, True, True, 8)
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        iou, d, med = float(np.float32(rng.uniform(0.7, 1.0))), float(np.float32(rng.uniform(0, 2))), \
+            float(np.float32(rng.uniform(1, 20)))
+        ref = C.is_new_keyframe(np.float32(iou), np.float32(d), np.float32(med), np.float32(0.9), np.float32(0.08))
+        assert B.s3gs_keyframe_is_new(p, iou, d, med) == ref
+    for _ in range(300):
+        n = int(rng.integers(0, 12))
+        ids = list(rng.permutation(100)[:n])
+        oc = [float(np.float32(x)) for x in rng.choice([0.1, 0.29, 0.3, 0.31, 0.5, 0.5, 0.7, 0.9], n)]
+        maxw = int(rng.integers(1, 10))
+        q = B.s3gs_keyframe_params_default(max_window=maxw)
+        ref = C.window_update(ids, [np.float32(x) for x in oc], 777, k_oc=np.float32(0.3), max_window=maxw)
+        assert B.s3gs_keyframe_window_update(q, ids, oc, 777) == ref
