@@ -52,12 +52,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--crop", default="32x24", help="oracle sample crop (w x h) of view 0")
-    ap.add_argument("--row", default="window", choices=["window", "align", "pose", "covis"],
+    ap.add_argument("--row", default="window", choices=["window", "align", "pose", "covis", "mapping"],
                     help="window: the mapping-window render step (default); align: scale alignment + "
                          "pointmap replacement of a 12-view window; pose: photometric pose refinement of "
                          "one frame against the config-3 map; covis: keyframe covisibility (IOU/OC) and median "
-                         "depths of the config-3 window")
+                         "depths of the config-3 window; mapping: full window-mapping iterations (render, loss, "
+                         "backward, fused Adam + L_iso, pose step)")
     ap.add_argument("--pose-iters", type=int, default=20, help="iterations per captured refinement (--row pose)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="--row pose: use the library's default schedule instead of autotuning it for the "
+                         "single-view workload first")
     return ap.parse_args()
 
 
@@ -723,11 +727,22 @@ def run_pose(args):
     if args.impl == "reference":
         return run_pose_reference(args, sc, true_cam, start_cam)
     torch.cuda.set_device(local)
-    R = Renderer(local)
+    tw, th = tile_shape(args.tile)
+    opt = B.s3gs_options_default(tile_w=tw, tile_h=th, blocks_per_sm=args.blocks_per_sm,
+                                 deterministic=args.deterministic, recompute=args.recompute)
+    for k, a in (("batch", args.batch), ("pixels_per_thread", args.ppt), ("bwd_pixels_per_thread", args.bppt)):
+        if a:
+            setattr(opt, k, a)
+    R = Renderer(local, opt)
     p = R.upload(sc)
     tgt = R.forward(p, [true_cam])["rgb"].clone()
+    tuned = None
+    if not args.no_autotune:
+        from paper_2507_03737_gb300.autotune import autotune, options_to_dict
+        opt = autotune(R, p, [start_cam], base=opt, repeats=3, rounds=2)
+        tuned = options_to_dict(opt)
     iters = args.pose_iters
-    pr = PoseRefiner(R, p, [start_cam], tgt, iters=iters)
+    pr = PoseRefiner(R, p, [start_cam], tgt, iters=iters, options=opt)
     pr.capture()
     for _ in range(max(3, args.warmup)):
         pr.run()
@@ -789,7 +804,9 @@ def run_pose(args):
             "data": "synthetic (seeded config-3 map, target = render at the true pose; no dataset)",
             "config": {"workload": f"config 3 map (1M Gaussians), view 0 (1241x376), {iters} iterations per "
                                    f"captured refinement, 3 cm / 1.4 deg initial error",
-                       "l2": "flushed (256 MB write) before every refinement", "graph": True},
+                       "l2": "flushed (256 MB write) before every refinement", "graph": True,
+                       "tile": f"{opt.tile_w}x{opt.tile_h}", "blocks_per_sm": int(opt.blocks_per_sm),
+                       "autotuned": tuned},
             "stages_ms_per_iteration": stages, "stages_timed_in": "eager iterations after the timed region",
             "pose_error_fro": {"start": err0, "after": err},
             "roofline": roof, "cpu_baseline": cpu,
@@ -938,8 +955,89 @@ def run_covis(args):
     return 0
 
 
+MAPPING_METRIC = ("window-mapping iterations/s (render + loss + backward + fused Adam/L_iso + pose step), "
+                  "1M Gaussians, 12×1241×376")
+
+
+def run_mapping(args):
+    import numpy as np
+    import torch
+
+    from paper_2507_03737_gb300 import binding as B
+    from paper_2507_03737_gb300 import scenes
+    from paper_2507_03737_gb300.autograd import Renderer
+    from paper_2507_03737_gb300.slam import MapOptimizer
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "metric": MAPPING_METRIC,
+                          "unavailable": "the FP64 oracle needs hours per window-mapping iteration; "
+                                         "see --impl reference of the default row"}), flush=True)
+        return 0
+    torch.cuda.set_device(local)
+    sc = scenes.config_scene(3)
+    V = len(sc.cameras)
+    R = Renderer(local)
+    tgt = R.forward(R.upload(scenes.perturb_scene(sc, 77)), sc.cameras)
+    t_rgb, t_pm = tgt["rgb"].clone(), tgt["pointmap"].clone()
+    p = R.upload(sc)
+    hp = B.s3gs_map_adam_default(lambda_iso=10.0 / (3 * sc.n))
+    frozen = torch.zeros(V, dtype=torch.uint8, device=R.device)
+    frozen[0] = 1
+    iters = 5
+    mo = MapOptimizer(R, p, sc.cameras, t_rgb, t_pointmap=t_pm, hp=hp, iters=iters, frozen=frozen)
+    mo.capture()
+    for _ in range(max(3, args.warmup)):
+        mo.run()
+    torch.cuda.synchronize()
+    mo.check()
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=R.device)
+    flush = lambda: flush_buf.zero_()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = statistics.mean(timed(mo.run, args.steps, flush))
+    clk = clocks.stop()
+    mo.check()
+    # the fused optimiser step alone
+    adam_ms = statistics.mean(timed(lambda: B.s3gs_map_adam_step(R.ctx, mo.p, mo.grads, mo.m, mo.v, mo.step, mo.hp),
+                                    max(3, args.steps), flush))
+    n_par = sum(int(mo.p[k].numel()) for k in B.MAP_TENSORS)
+    peaks, peak_src = measured_peaks()
+    ach = 28.0 * n_par / (adam_ms / 1e3) / 1e9
+    B.s3gs_set_timing(R.ctx, 1)
+    stage_tot = {}
+    for _ in range(3):
+        flush()
+        mo.iteration()
+        for k, v in B.s3gs_read_timing(R.ctx).items():
+            stage_tot[k] = stage_tot.get(k, 0.0) + v / 3
+    B.s3gs_set_timing(R.ctx, 0)
+    stage_tot["map_adam"] = adam_ms
+    line = {"metric": MAPPING_METRIC, "value": iters / (ms / 1e3), "unit": "iterations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "none (replicas only)", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded config-3 map, targets = renders of a perturbed copy; no dataset)",
+            "config": {"workload": f"config 3 window (1M Gaussians, 12 x 1241x376), {iters} mapping iterations per "
+                                   "graph replay, alpha = 0.98, lambda_iso = 10 / (3 |G|), first keyframe frozen",
+                       "l2": "flushed (256 MB write) before every replay", "graph": True},
+            "views_per_s": V * iters / (ms / 1e3),
+            "stages_ms_per_iteration": stage_tot, "stages_timed_in": "eager iterations after the timed region",
+            "roofline": {"kernel": "map_adam", "bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": ach / float(peaks["hbm_gbs"]), "traffic": None,
+                         "bytes_per_launch": 28 * n_par, "ms_per_launch": adam_ms, "peak_of": peak_src},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps * iters * 16, "clocks": clk,
+            "loss_last": float(mo.loss[0])}
+    print(json.dumps(line), flush=True)
+    R.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.row == "mapping":
+        return run_mapping(args)
     if args.row == "covis":
         return run_covis(args)
     if args.row == "align":

@@ -4,7 +4,7 @@
 // include/s3gs_slam.h).
 //
 // One alignment iteration is one pass over both pointmaps. A CTA stages a band
-// of P rows by ppc * P columns (ppc = 256 / P patches) of X^r and X^p in shared
+// of P rows by ppc * P columns (ppc = 128 / P patches) of X^r and X^p in shared
 // memory, computes the joint mean and population standard deviation of each
 // of its patches (mean first, then centred squares, both from shared memory),
 // gates the patches, tests every point of the candidate patches and reduces
@@ -23,7 +23,7 @@
 namespace s3gs {
 namespace {
 
-constexpr int kAlignThreads = 256;
+constexpr int kAlignThreads = 128;  // small CTAs: about 7 resident per SM at P = 10
 constexpr int kMaxDevices = 64;
 
 struct AlignView {
@@ -50,6 +50,16 @@ int align_ppc(int P) { return kAlignThreads / P; }
 size_t align_smem_bytes(int P) {
     const int ppc = align_ppc(P), maxc = ppc * P;
     return sizeof(float) * ((size_t)6 * P * maxc + 2 * (size_t)maxc + 4 * (size_t)ppc) + sizeof(int) * ppc;
+}
+
+// 4-byte asynchronous global -> shared copy (no register staging), and the
+// wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 __global__ void align_init_kernel(const float *sigma_init, float *sigma, int n_views) {
@@ -85,23 +95,27 @@ __global__ void __launch_bounds__(kAlignThreads)
     const int t = threadIdx.x;
     const bool col = t < ncols;
     const int j = t / P;  // patch of this thread's column
-    // Each thread loads its own column of both maps (coalesced across the warp
-    // for every channel and row), keeps it in shared memory and sums it.
+    // Each thread copies its own column of both maps into shared memory with
+    // asynchronous copies (coalesced across the warp for every channel and row;
+    // all of a thread's copies are in flight at once), then sums it.
     if (col) {
         const float *rc = Xr + 3 * vw.pix_base + (long long)y0 * vw.w + x0 + t;
         const float *pc = Xp + 3 * vw.pix_base + (long long)y0 * vw.w + x0 + t;
-        float a = 0.f, q = 0.f;
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll 4
+        for (int c = 0; c < 3; ++c)
             for (int y = 0; y < rows; ++y) {
                 const long long off = c * HW + (long long)y * vw.w;
-                const float xr = __ldg(rc + off), xp = __ldg(pc + off);
-                s_r[(c * P + y) * maxc + t] = xr;
-                s_p[(c * P + y) * maxc + t] = xp;
-                a += xr;
-                q += xp;
+                cp_async4(s_r + (c * P + y) * maxc + t, rc + off);
+                cp_async4(s_p + (c * P + y) * maxc + t, pc + off);
             }
-        }
+    }
+    cp_async_wait_all();
+    if (col) {
+        float a = 0.f, q = 0.f;
+        for (int c = 0; c < 3; ++c)
+            for (int y = 0; y < rows; ++y) {
+                a += s_r[(c * P + y) * maxc + t];
+                q += s_p[(c * P + y) * maxc + t];
+            }
         s_col[t] = a;
         s_col[maxc + t] = q;
     }

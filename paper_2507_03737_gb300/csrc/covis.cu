@@ -39,7 +39,13 @@ struct CovisArgs {
 __global__ void __launch_bounds__(kCovisThreads) covis_kernel(const __grid_constant__ CovisArgs a) {
     __shared__ unsigned s_b[kCovisThreads / 32][S3GS_MAX_VIEWS];
     __shared__ unsigned s_acc[kMaxPairs];
-    for (int p = threadIdx.x; p < a.n_pairs; p += kCovisThreads) s_acc[p] = 0u;
+    __shared__ unsigned char s_pi[kMaxPairs], s_pj[kMaxPairs];  // lane-varying indices: keep them out of the
+                                                                 // constant bank, which serialises them
+    for (int p = threadIdx.x; p < a.n_pairs; p += kCovisThreads) {
+        s_acc[p] = 0u;
+        s_pi[p] = a.pi[p];
+        s_pj[p] = a.pj[p];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned cnt[kPairSlots];
@@ -57,7 +63,7 @@ __global__ void __launch_bounds__(kCovisThreads) covis_kernel(const __grid_const
 #pragma unroll
         for (int k = 0; k < kPairSlots; ++k) {
             const int p = lane + 32 * k;
-            if (p < a.n_pairs) cnt[k] += __popc(s_b[warp][a.pi[p]] & s_b[warp][a.pj[p]]);
+            if (p < a.n_pairs) cnt[k] += __popc(s_b[warp][s_pi[p]] & s_b[warp][s_pj[p]]);
         }
         __syncwarp();
     }
@@ -68,7 +74,7 @@ __global__ void __launch_bounds__(kCovisThreads) covis_kernel(const __grid_const
     }
     __syncthreads();
     for (int p = threadIdx.x; p < a.n_pairs; p += kCovisThreads)
-        if (s_acc[p]) atomicAdd(&a.counts[a.pi[p] * a.V + a.pj[p]], (unsigned long long)s_acc[p]);
+        if (s_acc[p]) atomicAdd(&a.counts[s_pi[p] * a.V + s_pj[p]], (unsigned long long)s_acc[p]);
 }
 
 // Mirror the upper triangle and form IOU (Eq. S1) and OC (Eq. S2).

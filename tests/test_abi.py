@@ -79,8 +79,9 @@ def test_align_params_and_workspace_are_host_only(lib):
     assert abs(p.delta_mu - 0.3) < 1e-7 and abs(p.delta_sigma - 0.3) < 1e-7
     assert abs(p.eps_r - 0.1) < 1e-7 and abs(p.tau - 0.01) < 1e-9
     wh, nv = B.view_sizes([(1241, 376), (23, 7)])
-    # 1241x376 at P = 10: 38 patch rows x ceil(125 / 25) CTAs; 23x7: 1 x 1; 16 bytes per CTA
-    assert B.s3gs_scale_align_workspace(wh, nv, 10) == 16 * (38 * 5 + 1)
+    # 1241x376 at P = 10: 38 patch rows x ceil(125 / 12) CTAs (12 patches of a 128-thread CTA);
+    # 23x7: 1 x 1; 16 bytes per CTA
+    assert B.s3gs_scale_align_workspace(wh, nv, 10) == 16 * (38 * 11 + 1)
     for bad in (0, 33):
         with pytest.raises(B.S3GSError):
             B.s3gs_scale_align_workspace(wh, nv, bad)

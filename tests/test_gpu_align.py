@@ -3,7 +3,7 @@ and remedial factor against the FP64 oracle, on seeded synthetic pointmaps.
 
 Tolerances (derived from the FP32 arithmetic of the kernels):
   * scale factor: 2e-5 relative. The kernel sums each CTA's correct points in
-    FP32 (at most 3 P rows per thread, then a 5-level warp tree and 8 warps:
+    FP32 (at most 3 P rows per thread, then a 5-level warp tree and 4 warps:
     about 46 roundings of 2^-24 in the worst case for each sum) and the CTAs
     in double, so each sum is within ~3e-6 relative and their ratio within ~6e-6.
   * decisions (candidate patches, correct points, replaced points) are FP32 on
