@@ -225,13 +225,18 @@ s3gs_status s3gs_mapping_loss_noalloc(const s3gs_camera *cams, int32_t n_views, 
  * s3gs_debug_records: per record r = v * n + g of the last forward:
  *   xy [r][2], conic_opacity [r][4] (A, B, C, opacity), rgb_depth [r][4]
  *   (r, g, b, view-space z), extent [r][2] (integer half-extents rx, ry of the
- *   tile cover, 0 = culled). n_records must equal n_views * n.
+ *   bounding rectangle of the tile cover, 0 = culled). n_records must equal
+ *   n_views * n.
  * s3gs_debug_binning: the tile-sorted duplicate list as 64-bit keys
  *   (global tile id << 32 | float bits of z), values (Gaussian index g) and
  *   per-tile ranges [n_tiles + 1]; *n_tiles and *n_dup receive the sizes (pass
  *   NULL arrays first to query them). */
 s3gs_status s3gs_debug_records(s3gs_ctx *ctx, s3gs_state *state, int64_t n_records, float *xy,
                                float *conic_opacity, float *rgb_depth, int32_t *extent);
+/* s3gs_debug_cover: per record the bound q_cover of its tile cover (the record
+ * is listed in a tile iff its ellipse A dx^2 + 2 B dx dy + C dy^2 <= q_cover
+ * meets the box of the tile's pixel centres; 0 for culled records). */
+s3gs_status s3gs_debug_cover(s3gs_ctx *ctx, s3gs_state *state, int64_t n_records, float *q_cover);
 s3gs_status s3gs_debug_binning(s3gs_ctx *ctx, s3gs_state *state, uint64_t *keys,
                                uint32_t *values, int64_t *ranges, int64_t *n_tiles,
                                int64_t *n_dup);

@@ -60,7 +60,7 @@ def lib():
                                         ctypes.c_int, _D, ctypes.c_double, _D,
                                         _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
             L.or_bin_referee.argtypes = [ctypes.c_int64, ctypes.c_int, _I32, ctypes.c_int,
-                                         ctypes.c_int, _F, _F, _I32, _I32, _F, _U64, _U32, _I64]
+                                         ctypes.c_int, _F, _F, _I32, _I32, _F, _F, _F, _U64, _U32, _I64]
             L.or_bin_referee.restype = ctypes.c_int64
             L.or_num_threads.restype = ctypes.c_int
             L.or_set_guard.argtypes = [ctypes.c_double]
@@ -171,23 +171,27 @@ def render_bwd(scene, d_rgb=None, d_depth=None, d_pointmap=None, d_alpha=None, c
     return out
 
 
-def bin_referee(view_wh, tile_w, tile_h, u, v, rx, ry, z):
-    """Integer referee: stable (tile, depth) keys, values and per-tile ranges."""
+def bin_referee(view_wh, tile_w, tile_h, u, v, rx, ry, z, conic=None, q_cover=None):
+    """Integer referee: stable (tile, depth) keys, values and per-tile ranges.
+    conic ([records][3] = A, B, C) and q_cover ([records]) enable the ellipse
+    test of the tile cover; without them every tile of the rectangle is listed."""
     n_views = len(view_wh)
     wh = np.ascontiguousarray(np.asarray(view_wh, dtype=np.int32).reshape(n_views, 2))
     u = np.ascontiguousarray(u, dtype=np.float32); v = np.ascontiguousarray(v, dtype=np.float32)
     rx = np.ascontiguousarray(rx, dtype=np.int32); ry = np.ascontiguousarray(ry, dtype=np.int32)
     z = np.ascontiguousarray(z, dtype=np.float32)
+    cn = None if conic is None else np.ascontiguousarray(np.asarray(conic, dtype=np.float32).reshape(-1, 3))
+    qc = None if q_cover is None else np.ascontiguousarray(q_cover, dtype=np.float32)
     n = u.size // n_views
     L = lib()
     K = L.or_bin_referee(n, n_views, _p(wh, _I32), tile_w, tile_h, _p(u, _F), _p(v, _F),
-                         _p(rx, _I32), _p(ry, _I32), _p(z, _F), None, None, None)
+                         _p(rx, _I32), _p(ry, _I32), _p(z, _F), _p(cn, _F), _p(qc, _F), None, None, None)
     assert K >= 0
     n_tiles = sum(((w + tile_w - 1) // tile_w) * ((h + tile_h - 1) // tile_h) for w, h in wh)
     keys = np.zeros(max(K, 1), dtype=np.uint64); vals = np.zeros(max(K, 1), dtype=np.uint32)
     ranges = np.zeros(n_tiles + 1, dtype=np.int64)
     K2 = L.or_bin_referee(n, n_views, _p(wh, _I32), tile_w, tile_h, _p(u, _F), _p(v, _F),
-                          _p(rx, _I32), _p(ry, _I32), _p(z, _F), _p(keys, _U64), _p(vals, _U32),
-                          _p(ranges, _I64))
+                          _p(rx, _I32), _p(ry, _I32), _p(z, _F), _p(cn, _F), _p(qc, _F), _p(keys, _U64),
+                          _p(vals, _U32), _p(ranges, _I64))
     assert K2 == K
     return keys[:K], vals[:K], ranges

@@ -744,11 +744,44 @@ int or_render_bwd(int64_t n, int sh_degree, const double *means, const double *l
  * their stable sort and the per-tile ranges. Definition: a visible record
  * (view v, Gaussian g) with centre (u, v) and integer half-extents (rx, ry)
  * covers pixel columns [ceil(u - rx), floor(u + rx)] and rows
- * [ceil(v - ry), floor(v + ry)] (FP32 arithmetic), clipped to the view; it is
- * emitted once for every tile of tw x th pixels that this rectangle touches,
- * in row-major tile order, with key (global tile id << 32) | bits(z) and value
- * g. Global tile ids number the tiles of view 0 first, row-major, then view 1,
- * and so on. Keys are sorted stably, so equal keys keep ascending g. */
+ * [ceil(v - ry), floor(v + ry)] (FP32 arithmetic), clipped to the view. Of the
+ * tiles of tw x th pixels that this rectangle touches, the record is listed in
+ * those whose box of pixel centres (inside the view) meets its ellipse
+ * q(d) = A dx^2 + 2 B dx dy + C dy^2 <= q_cover (when conic and q_cover are
+ * given; else in all of them): the smallest q over the box is 0 if the centre
+ * lies in the box, else the least of the four edges' clamped one-dimensional
+ * minima, evaluated in FP32 in the order written below. It is emitted once per
+ * listed tile, in row-major tile order, with key (global tile id << 32) |
+ * bits(z) and value g. Global tile ids number the tiles of view 0 first,
+ * row-major, then view 1, and so on. Keys are sorted stably, so equal keys
+ * keep ascending g. */
+static float or_edge_min_q(float a, float b, float c, float x, float lo, float hi) {
+    /* min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0) */
+    float y = -(b * x) / c;
+    y = fminf(fmaxf(y, lo), hi);
+    float t1 = a * (x * x);
+    float t2 = (2.0f * b) * (x * y);
+    float t3 = c * (y * y);
+    return (t1 + t2) + t3;
+}
+
+static int or_tile_hit(float u, float v, float A, float B, float C, float qc, int px0, int px1, int py0, int py1) {
+    float dx0 = (float)px0 - u, dx1 = (float)px1 - u, dy0 = (float)py0 - v, dy1 = (float)py1 - v;
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return qc >= 0.0f;
+    float m = or_edge_min_q(A, B, C, dx0, dy0, dy1);
+    m = fminf(m, or_edge_min_q(A, B, C, dx1, dy0, dy1));
+    m = fminf(m, or_edge_min_q(C, B, A, dy0, dx0, dx1));
+    m = fminf(m, or_edge_min_q(C, B, A, dy1, dx0, dx1));
+    return m <= qc;
+}
+
+static int or_listed(const float *conic, const float *qcover, int64_t r, float u, float v, int tx, int ty, int tw,
+                     int th, int W, int H) {
+    if (!conic || !qcover) return 1;
+    int px0 = tx * tw, px1 = px0 + tw - 1 < W - 1 ? px0 + tw - 1 : W - 1;
+    int py0 = ty * th, py1 = py0 + th - 1 < H - 1 ? py0 + th - 1 : H - 1;
+    return or_tile_hit(u, v, conic[3 * r], conic[3 * r + 1], conic[3 * r + 2], qcover[r], px0, px1, py0, py1);
+}
 typedef struct {
     uint64_t key;
     int64_t order;
@@ -778,7 +811,8 @@ static int or_rect(float u, float v, int rx, int ry, int W, int H, int tw, int t
  * tile ranges (n_tiles_total + 1 entries). Returns K or a negative error. */
 int64_t or_bin_referee(int64_t n, int n_views, const int32_t *view_wh, int tw, int th,
                        const float *u, const float *v, const int32_t *rx, const int32_t *ry,
-                       const float *z, uint64_t *out_keys, uint32_t *out_values, int64_t *out_ranges) {
+                       const float *z, const float *conic, const float *qcover, uint64_t *out_keys,
+                       uint32_t *out_values, int64_t *out_ranges) {
     int64_t *tile_base = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_views + 1));
     if (!tile_base) return -5;
     int64_t acc = 0;
@@ -796,7 +830,8 @@ int64_t or_bin_referee(int64_t n, int n_views, const int32_t *view_wh, int tw, i
             int64_t r = (int64_t)vv * n + g;
             int a, b, c, d;
             if (!or_rect(u[r], v[r], rx[r], ry[r], W, H, tw, th, &a, &b, &c, &d)) continue;
-            K += (int64_t)(c - a + 1) * (d - b + 1);
+            for (int ty = b; ty <= d; ++ty)
+                for (int tx = a; tx <= c; ++tx) K += or_listed(conic, qcover, r, u[r], v[r], tx, ty, tw, th, W, H);
         }
     }
     if (!out_keys) { free(tile_base); return K; }
@@ -814,6 +849,7 @@ int64_t or_bin_referee(int64_t n, int n_views, const int32_t *view_wh, int tw, i
             memcpy(&zb, &z[r], 4);
             for (int ty = b; ty <= d; ++ty)
                 for (int tx = a; tx <= c; ++tx) {
+                    if (!or_listed(conic, qcover, r, u[r], v[r], tx, ty, tw, th, W, H)) continue;
                     uint64_t tile = (uint64_t)(tile_base[vv] + (int64_t)ty * tiles_x + tx);
                     kv[e].key = (tile << 32) | zb;
                     kv[e].order = e;

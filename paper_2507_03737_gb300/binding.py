@@ -20,7 +20,7 @@ __all__ = [
     "Options", "lib", "s3gs_options_default", "s3gs_create", "s3gs_destroy", "s3gs_last_error",
     "s3gs_state_create", "s3gs_state_destroy", "s3gs_reserve", "s3gs_render_fwd",
     "s3gs_render_bwd", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_debug_records",
-    "s3gs_debug_binning", "s3gs_set_counting", "s3gs_read_counters", "s3gs_version",
+    "s3gs_debug_binning", "s3gs_debug_cover", "s3gs_set_counting", "s3gs_read_counters", "s3gs_version",
     "s3gs_set_timing", "s3gs_read_timing", "STAGES", "s3gs_mapping_loss_noalloc",
     "make_cameras", "make_gaussians", "check", "AlignParams", "s3gs_align_params_default",
     "s3gs_scale_align_workspace", "s3gs_scale_align", "s3gs_pointmap_replace", "s3gs_scale_remedy", "view_sizes",
@@ -114,6 +114,7 @@ def _load():
                                              _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                              _P, _P, _P, _P, _P]),
         "s3gs_debug_records": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+        "s3gs_debug_cover": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
         "s3gs_debug_binning": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64),
                                               ctypes.POINTER(ctypes.c_int64)]),
         "s3gs_set_counting": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -307,6 +308,13 @@ def s3gs_debug_records(ctx, state, n_records):
     check(ctx, lib().s3gs_debug_records(ctx, state, int(n_records), xy.ctypes.data, co.ctypes.data,
                                         rz.ctypes.data, ext.ctypes.data))
     return dict(xy=xy, conic_opacity=co, rgb_depth=rz, extent=ext)
+
+
+def s3gs_debug_cover(ctx, state, n_records):
+    import numpy as np
+    q = np.zeros(n_records, np.float32)
+    check(ctx, lib().s3gs_debug_cover(ctx, state, int(n_records), q.ctypes.data))
+    return q
 
 
 def s3gs_debug_binning(ctx, state):

@@ -666,6 +666,27 @@ s3gs_status s3gs_debug_records(s3gs_ctx *ctx, s3gs_state *st, int64_t n_records,
     return S3GS_OK;
 }
 
+s3gs_status s3gs_debug_cover(s3gs_ctx *ctx, s3gs_state *st, int64_t n_records, float *q_cover) {
+    if (!ctx || !st || !st->valid) return fail(ctx, S3GS_E_STATE, "debug_cover: no forward on this state");
+    long long nr = st->g.n * st->vb.n_views;
+    if (n_records != nr || !q_cover) return fail(ctx, S3GS_E_INVALID, "debug_cover: n_records must be n_views * n");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(st->stream), "sync");
+    if (nr == 0) return S3GS_OK;
+    // the bound is the fourth float of each record's third float4 (stride 12 floats)
+    CK(cudaMemcpy2D(q_cover, sizeof(float), reinterpret_cast<const char *>(st->rec.p) + 11 * sizeof(float),
+                    sizeof(Record), sizeof(float), (size_t)nr, cudaMemcpyDeviceToHost),
+       "debug_cover");
+    int2 *e = (int2 *)malloc(sizeof(int2) * nr);
+    if (!e) return fail(ctx, S3GS_E_NOMEM, "debug_cover: host allocation");
+    cudaError_t err = cudaMemcpy(e, st->ext.p, sizeof(int2) * nr, cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) { free(e); return cuda_fail(ctx, err, "debug_cover"); }
+    for (long long r = 0; r < nr; ++r)
+        if (e[r].x <= 0) q_cover[r] = 0.f;
+    free(e);
+    return S3GS_OK;
+}
+
 s3gs_status s3gs_debug_binning(s3gs_ctx *ctx, s3gs_state *st, uint64_t *keys, uint32_t *values, int64_t *ranges,
                                int64_t *n_tiles, int64_t *n_dup) {
     if (!ctx || !st || !st->valid) return fail(ctx, S3GS_E_STATE, "debug_binning: no forward on this state");

@@ -222,16 +222,24 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                         }
                     }
                     Record R;
+                    const float lo2 = log2f(A.opacity);
+                    const float qc = fminf(kCutoffQ, 2.0f * kLn2 * (lo2 - kSkipL)) * (1.0f + 2e-5f + 8e-7f * kappa);
                     R.a = make_float4(u, vv, cc * idet, -cb * idet);
-                    R.b = make_float4(ca * idet, A.opacity, pz, log2f(A.opacity));
-                    R.c = make_float4(col[0], col[1], col[2], 0.f);
+                    R.b = make_float4(ca * idet, A.opacity, pz, lo2);
+                    R.c = make_float4(col[0], col[1], col[2], qc);
                     a.rec[r] = R;
                     ext = make_int2(rx, ry);
                     mask |= 1u << v;
                     const int bin = depth_bin(pz);
-                    for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx)
-                            atomicAdd(a.tile_count + (size_t)(vi.tile_base + ty * vi.tiles_x + tx) * kDepthBins + bin, 1u);
+                    for (int ty = ty0; ty <= ty1; ++ty) {
+                        const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
+                        for (int tx = tx0; tx <= tx1; ++tx) {
+                            const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
+                            if (tile_hit(u, vv, R.a.z, R.a.w, R.b.x, qc, px0, px1, py0, py1))
+                                atomicAdd(a.tile_count + (size_t)(vi.tile_base + ty * vi.tiles_x + tx) * kDepthBins + bin,
+                                          1u);
+                        }
+                    }
                 }
             }
         }

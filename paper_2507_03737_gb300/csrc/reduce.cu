@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(256) twist_reduce_kernel(const TwistReduceArgs
 }
 
 // Deterministic mode: each visible record gathers its per-tile partials, tile
-// by tile in row-major order; its position inside each tile's list is found by
-// binary search of its unique (depth bits, index) key.
+// by tile in row-major order over the tiles its cover lists it in; its position
+// inside each tile's list is found by binary search of its unique (depth bits,
+// index) key.
 __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, const __grid_constant__ ViewBatch vb) {
     long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long total = (long long)vb.n_views * a.n;
@@ -57,8 +58,12 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
     float acc[kGrad2d];
 #pragma unroll
     for (int q = 0; q < kGrad2d; ++q) acc[q] = 0.f;
+    const float C = a.rec[r].b.x, qc = a.rec[r].c.w;
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
+            const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
+            const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
+            if (!tile_hit(ra.x, ra.y, ra.z, ra.w, C, qc, px0, px1, py0, py1)) continue;  // not listed there
             int t = vi.tile_base + ty * vi.tiles_x + tx;
             unsigned lo = a.tile_start[t * kDepthBins], hi = a.tile_start[(t + 1) * kDepthBins];
             while (lo < hi) {

@@ -67,8 +67,41 @@ struct ViewBatch {
 struct __align__(16) Record {
     float4 a;  // u, v, A, B  (conic = [[A, B], [B, C]])
     float4 b;  // C, opacity, z, log2(opacity)
-    float4 c;  // r, g, b, unused
+    float4 c;  // r, g, b, q_cover (the tile-cover bound on q, see tile_hit)
 };
+
+// Tile cover. A record is listed in a tile only if its ellipse q(d) <= q_cover,
+// q(d) = A dx^2 + 2 B dx dy + C dy^2, meets the box spanned by the centres of
+// the tile's pixels inside the image. q_cover is the largest q at which the
+// blend can accept a pair -- min(9, 2 ln 2 (log2 opacity - log2(1/255))), the
+// 3-sigma cutoff or the 1/255 skip -- widened for FP32 rounding of the conic
+// (relative 2e-5 plus 8e-7 times its condition number). The smallest q over
+// the box lies on its border unless the centre is inside; on each edge it is a
+// clamped one-dimensional minimum. Every operation is an explicit
+// round-to-nearest intrinsic, so the projection's counts, the emission and the
+// deterministic reduce take identical decisions (and the integer referee can
+// repeat them in plain C).
+__device__ __forceinline__ float edge_min_q(float a, float b, float c, float x, float lo, float hi) {
+    // min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0)
+    float y = __fdiv_rn(-__fmul_rn(b, x), c);
+    y = fminf(fmaxf(y, lo), hi);
+    const float t1 = __fmul_rn(a, __fmul_rn(x, x));
+    const float t2 = __fmul_rn(__fmul_rn(2.0f, b), __fmul_rn(x, y));
+    const float t3 = __fmul_rn(c, __fmul_rn(y, y));
+    return __fadd_rn(__fadd_rn(t1, t2), t3);
+}
+
+__device__ __forceinline__ bool tile_hit(float u, float v, float A, float B, float C, float qc, int px0, int px1,
+                                         int py0, int py1) {
+    const float dx0 = __fsub_rn((float)px0, u), dx1 = __fsub_rn((float)px1, u);
+    const float dy0 = __fsub_rn((float)py0, v), dy1 = __fsub_rn((float)py1, v);
+    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return qc >= 0.f;
+    float m = edge_min_q(A, B, C, dx0, dy0, dy1);
+    m = fminf(m, edge_min_q(A, B, C, dx1, dy0, dy1));
+    m = fminf(m, edge_min_q(C, B, A, dy0, dx0, dx1));
+    m = fminf(m, edge_min_q(C, B, A, dy1, dx0, dx1));
+    return m <= qc;
+}
 
 struct DevCounters {
     unsigned long long n_dup;     // total (Gaussian, tile) pairs K of the last forward

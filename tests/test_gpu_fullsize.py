@@ -167,3 +167,21 @@ def test_config5_crop_deterministic_vs_atomic(R):
     again = R.backward_np(ups, 1)
     for k in again:
         np.testing.assert_array_equal(again[k], grads[1][k])
+
+
+def test_config3_binning_bit_exact_at_full_size(R):
+    """The whole config-3 duplicate list (every tile of 12 x 1241x376) equals the
+    integer referee's stable sort of the same records' cover, bit for bit."""
+    from paper_2507_03737_gb300 import binding as B
+    sc = scenes.config_scene(3)
+    R.render_np(sc)
+    V = len(sc.cameras)
+    rec = B.s3gs_debug_records(R.ctx, R.state, V * sc.n)
+    qc = B.s3gs_debug_cover(R.ctx, R.state, V * sc.n)
+    keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
+    wh = [(c["width"], c["height"]) for c in sc.cameras]
+    rk, rv, rr = O.bin_referee(wh, 16, 16, rec["xy"][:, 0], rec["xy"][:, 1], rec["extent"][:, 0],
+                               rec["extent"][:, 1], rec["rgb_depth"][:, 3], conic=rec["conic_opacity"][:, :3],
+                               q_cover=qc)
+    assert keys.size == rk.size > 10_000_000
+    assert np.array_equal(keys, rk) and np.array_equal(vals, rv) and np.array_equal(ranges, rr)

@@ -62,8 +62,10 @@ def test_binning_bit_exact(R, tile):
     rec = B.s3gs_debug_records(R.ctx, R.state, sc.n * 3)
     keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
     wh = [(c["width"], c["height"]) for c in sc.cameras]
+    qc = B.s3gs_debug_cover(R.ctx, R.state, sc.n * 3)
     rk, rv, rr = O.bin_referee(wh, tile[0], tile[1], rec["xy"][:, 0], rec["xy"][:, 1], rec["extent"][:, 0],
-                               rec["extent"][:, 1], rec["rgb_depth"][:, 3])
+                               rec["extent"][:, 1], rec["rgb_depth"][:, 3], conic=rec["conic_opacity"][:, :3],
+                               q_cover=qc)
     assert keys.size == rk.size > 0
     assert np.array_equal(keys, rk)
     assert np.array_equal(vals, rv)
@@ -222,8 +224,10 @@ def test_heavy_tile_sort_path(R):
     keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
     assert np.diff(ranges).max() > 4096
     rec = B.s3gs_debug_records(R.ctx, R.state, n)
+    qc = B.s3gs_debug_cover(R.ctx, R.state, n)
     rk, rv, rr = O.bin_referee([(32, 32)], 16, 16, rec["xy"][:, 0], rec["xy"][:, 1], rec["extent"][:, 0],
-                               rec["extent"][:, 1], rec["rgb_depth"][:, 3])
+                               rec["extent"][:, 1], rec["rgb_depth"][:, 3], conic=rec["conic_opacity"][:, :3],
+                               q_cover=qc)
     assert np.array_equal(keys, rk) and np.array_equal(vals, rv) and np.array_equal(ranges, rr)
     # a deliberately dense stack: more pixels sit near a threshold than in the workloads
     compare_forward(gpu, O.render_fwd(sc), sc.cameras, max_excluded=0.05)

@@ -64,3 +64,66 @@ def test_referee_empty_and_offscreen():
     rx = np.int32([3, 3]); ry = np.int32([3, 3]); z = np.float32([1.0, 1.0])
     keys, vals, ranges = O.bin_referee([(32, 16)], 16, 16, u, v, rx, ry, z)
     assert keys.size == 0 and np.all(ranges == 0)
+
+
+def _golden_min(f, lo, hi, iters=200):
+    """Minimum of a convex function on [lo, hi] by golden-section search."""
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    a, b = lo, hi
+    c, d = b - g * (b - a), a + g * (b - a)
+    for _ in range(iters):
+        if f(c) < f(d):
+            b = d
+        else:
+            a = c
+        c, d = b - g * (b - a), a + g * (b - a)
+    return min(f(lo), f(hi), f(0.5 * (a + b)))
+
+
+def test_ellipse_cover_against_numerical_box_minimum():
+    """The ellipse test of the tile cover, checked per (record, tile) against an
+    FP64 minimum of q over the tile's box of pixel centres found by golden-section
+    search along the four edges (and 0 when the centre is inside); decisions
+    within 1e-4 (relative) of q_cover are not compared."""
+    rng = np.random.default_rng(11)
+    W, H, tw, th = 64, 48, 16, 8
+    n = 300
+    u = rng.uniform(-6, W + 6, n).astype(np.float32)
+    v = rng.uniform(-6, H + 6, n).astype(np.float32)
+    conic = np.zeros((n, 3), np.float32)
+    rx = np.zeros(n, np.int32); ry = np.zeros(n, np.int32)
+    for i in range(n):
+        s1, s2 = rng.uniform(0.8, 9.0, 2)
+        th_ = rng.uniform(0, math.pi)
+        R = np.array([[math.cos(th_), -math.sin(th_)], [math.sin(th_), math.cos(th_)]])
+        cov = R @ np.diag([s1 * s1, s2 * s2]) @ R.T
+        con = np.linalg.inv(cov)
+        conic[i] = [con[0, 0], con[0, 1], con[1, 1]]
+        rx[i] = math.ceil(3.0 * math.sqrt(cov[0, 0]) + 0.01)
+        ry[i] = math.ceil(3.0 * math.sqrt(cov[1, 1]) + 0.01)
+    qc = rng.uniform(2.0, 9.0, n).astype(np.float32)
+    z = np.float32(1.0) + np.arange(n, dtype=np.float32)
+    keys, vals, _ = O.bin_referee([(W, H)], tw, th, u, v, rx, ry, z, conic=conic, q_cover=qc)
+    listed = {(int(g), int(k >> np.uint64(32))) for k, g in zip(keys, vals)}
+    rect_keys, rect_vals, _ = O.bin_referee([(W, H)], tw, th, u, v, rx, ry, z)
+    compared = dropped = 0
+    for k, g in zip(rect_keys, rect_vals):
+        g = int(g); t = int(k >> np.uint64(32))
+        tx, ty = t % math.ceil(W / tw), t // math.ceil(W / tw)
+        px0, px1 = tx * tw, min(tx * tw + tw - 1, W - 1)
+        py0, py1 = ty * th, min(ty * th + th - 1, H - 1)
+        A, B, C = (float(x) for x in conic[g])
+        uu, vv = float(u[g]), float(v[g])
+        q = lambda x, y: A * (x - uu) ** 2 + 2 * B * (x - uu) * (y - vv) + C * (y - vv) ** 2
+        if px0 <= uu <= px1 and py0 <= vv <= py1:
+            m = 0.0
+        else:
+            m = min(_golden_min(lambda y: q(px0, y), py0, py1), _golden_min(lambda y: q(px1, y), py0, py1),
+                    _golden_min(lambda x: q(x, py0), px0, px1), _golden_min(lambda x: q(x, py1), px0, px1))
+        if abs(m - float(qc[g])) <= 1e-4 * float(qc[g]):
+            continue
+        compared += 1
+        hit = m <= float(qc[g])
+        dropped += not hit
+        assert ((g, t) in listed) == hit, (g, t, m, float(qc[g]))
+    assert compared > 500 and dropped > 50
