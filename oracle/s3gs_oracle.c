@@ -750,14 +750,15 @@ int or_render_bwd(int64_t n, int sh_degree, const double *means, const double *l
  * q(d) = A dx^2 + 2 B dx dy + C dy^2 <= q_cover (when conic and q_cover are
  * given; else in all of them): the smallest q over the box is 0 if the centre
  * lies in the box, else the least of the four edges' clamped one-dimensional
- * minima, evaluated in FP32 in the order written below. It is emitted once per
+ * minima (stationary points from the reciprocals 1/A and 1/C), evaluated in
+ * FP32 in the order written below. It is emitted once per
  * listed tile, in row-major tile order, with key (global tile id << 32) |
  * bits(z) and value g. Global tile ids number the tiles of view 0 first,
  * row-major, then view 1, and so on. Keys are sorted stably, so equal keys
  * keep ascending g. */
-static float or_edge_min_q(float a, float b, float c, float x, float lo, float hi) {
-    /* min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0) */
-    float y = -(b * x) / c;
+static float or_edge_min_q(float a, float b, float c, float ic, float x, float lo, float hi) {
+    /* min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0, ic = 1 / c) */
+    float y = -(b * x) * ic;
     y = fminf(fmaxf(y, lo), hi);
     float t1 = a * (x * x);
     float t2 = (2.0f * b) * (x * y);
@@ -767,11 +768,12 @@ static float or_edge_min_q(float a, float b, float c, float x, float lo, float h
 
 static int or_tile_hit(float u, float v, float A, float B, float C, float qc, int px0, int px1, int py0, int py1) {
     float dx0 = (float)px0 - u, dx1 = (float)px1 - u, dy0 = (float)py0 - v, dy1 = (float)py1 - v;
+    float iA = 1.0f / A, iC = 1.0f / C;
     if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return qc >= 0.0f;
-    float m = or_edge_min_q(A, B, C, dx0, dy0, dy1);
-    m = fminf(m, or_edge_min_q(A, B, C, dx1, dy0, dy1));
-    m = fminf(m, or_edge_min_q(C, B, A, dy0, dx0, dx1));
-    m = fminf(m, or_edge_min_q(C, B, A, dy1, dx0, dx1));
+    float m = or_edge_min_q(A, B, C, iC, dx0, dy0, dy1);
+    m = fminf(m, or_edge_min_q(A, B, C, iC, dx1, dy0, dy1));
+    m = fminf(m, or_edge_min_q(C, B, A, iA, dy0, dx0, dx1));
+    m = fminf(m, or_edge_min_q(C, B, A, iA, dy1, dx0, dx1));
     return m <= qc;
 }
 

@@ -122,8 +122,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const ScanArgs a) {
 __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __grid_constant__ ViewBatch vb) {
     __shared__ unsigned s_incl[8][32], s_excl[8][32], s_origin[8][32], s_ntx[8][32], s_tx[8][32];
     __shared__ unsigned long long s_key[8][32];
-    __shared__ float4 s_ell[8][32];  // u, v, A, B of the source record
-    __shared__ float2 s_ell2[8][32];  // C, q_cover
+    __shared__ CoverEllipse s_ell[8][32];  // cover ellipse of the source record
     __shared__ unsigned s_t0[8][32];  // tx0 | ty0 << 16
     __shared__ unsigned s_view[8][32];
     if (a.ctr->overflow) return;
@@ -132,8 +131,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
     const long long total = (long long)vb.n_views * a.n;
     unsigned cnt = 0, origin = 0, ntx = 1, tiles_x = 0, t0 = 0, view = 0;
     unsigned long long key = 0;
-    float4 ell = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 ell2 = make_float2(0.f, 0.f);
+    CoverEllipse ell;
+    ell.u = ell.v = ell.A = ell.B = ell.C = ell.iA = ell.iC = ell.qc = 0.f;
     if (r < total) {
         const int2 ext = a.ext[r];
         if (ext.x > 0) {
@@ -143,8 +142,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
             const float4 ra = a.rec[r].a;
             const float4 rb = a.rec[r].b;
             const float z = rb.z;
-            ell = ra;
-            ell2 = make_float2(rb.x, a.rec[r].c.w);
+            ell = cover_ellipse(ra.x, ra.y, ra.z, ra.w, rb.x, a.rec[r].c.w);
             view = (unsigned)v;
             const float x0 = ceilf(__fsub_rn(ra.x, (float)ext.x)), x1 = floorf(__fadd_rn(ra.x, (float)ext.x));
             const float y0 = ceilf(__fsub_rn(ra.y, (float)ext.y)), y1 = floorf(__fadd_rn(ra.y, (float)ext.y));
@@ -175,7 +173,6 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
     s_tx[warp][lane] = tiles_x;
     s_key[warp][lane] = key;
     s_ell[warp][lane] = ell;
-    s_ell2[warp][lane] = ell2;
     s_t0[warp][lane] = t0;
     s_view[warp][lane] = view;
     __syncwarp();
@@ -199,9 +196,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
                 const ViewInfo &vi = vb.v[s_view[warp][src]];
                 const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
                 const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
-                const float4 e = s_ell[warp][src];
-                const float2 e2 = s_ell2[warp][src];
-                if (tile_hit(e.x, e.y, e.z, e.w, e2.x, e2.y, px0, px1, py0, py1)) {
+                if (tile_hit(s_ell[warp][src], px0, px1, py0, py1)) {
                     const unsigned bucket = s_origin[warp][src] + row * s_tx[warp][src] + colm * kDepthBins;
                     pos[u] = atomicAdd(a.cursor + bucket, 1u);
                     kk[u] = s_key[warp][src];

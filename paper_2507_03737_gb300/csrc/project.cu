@@ -143,17 +143,69 @@ __device__ __forceinline__ void cam_centre(const float T[12], float c[3]) {
     for (int i = 0; i < 3; ++i) c[i] = -(T[i] * T[3] + T[4 + i] * T[7] + T[8 + i] * T[11]);
 }
 
+// Counts the (tile, depth bin) buckets of the 32 records a warp has just made
+// for one view: an inclusive warp scan numbers the records' candidate tiles
+// (their bounding rectangles), and in each round every lane takes one
+// candidate, fetches its record's cover ellipse with shuffles, tests it and
+// counts it. All lanes stay busy whatever the mix of record sizes.
+__device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const ViewBatch &vb, const ViewInfo &vi,
+                                                 bool has, const CoverEllipse &ell, int tx0, int ty0, int ntx, int nty,
+                                                 int bin) {
+    const int lane = threadIdx.x & 31;
+    const unsigned cnt = has ? (unsigned)(ntx * nty) : 0u;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned excl = incl - cnt;
+    const unsigned t0 = (unsigned)tx0 | ((unsigned)ty0 << 16);
+    for (unsigned base = 0; base < total; base += 32) {
+        const unsigned j = base + lane;
+        int src = 0;
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1)
+            if (__shfl_sync(0xffffffffu, incl, src + b - 1) <= j) src += b;
+        src = src > 31 ? 31 : src;
+        CoverEllipse e;
+        e.u = __shfl_sync(0xffffffffu, ell.u, src);
+        e.v = __shfl_sync(0xffffffffu, ell.v, src);
+        e.A = __shfl_sync(0xffffffffu, ell.A, src);
+        e.B = __shfl_sync(0xffffffffu, ell.B, src);
+        e.C = __shfl_sync(0xffffffffu, ell.C, src);
+        e.iA = __shfl_sync(0xffffffffu, ell.iA, src);
+        e.iC = __shfl_sync(0xffffffffu, ell.iC, src);
+        e.qc = __shfl_sync(0xffffffffu, ell.qc, src);
+        const unsigned s_excl = __shfl_sync(0xffffffffu, excl, src);
+        const unsigned s_t0 = __shfl_sync(0xffffffffu, t0, src);
+        const int s_ntx = __shfl_sync(0xffffffffu, ntx, src);
+        const int s_bin = __shfl_sync(0xffffffffu, bin, src);
+        if (j < total) {
+            const int local = (int)(j - s_excl);
+            const int tx = (int)(s_t0 & 0xffffu) + local % s_ntx, ty = (int)(s_t0 >> 16) + local / s_ntx;
+            const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
+            const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
+            if (tile_hit(e, px0, px1, py0, py1))
+                atomicAdd(a.tile_count + (size_t)(vi.tile_base + ty * vi.tiles_x + tx) * kDepthBins + s_bin, 1u);
+        }
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const __grid_constant__ ViewBatch vb) {
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.n) return;
+    // every lane stays to the end: the tile counting below is warp-cooperative
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = gid < a.n;
+    const long long g = live ? gid : 0;
     constexpr int NC = (D + 1) * (D + 1);
     float m[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
     float ls[3] = {a.log_scales[3 * g], a.log_scales[3 * g + 1], a.log_scales[3 * g + 2]};
     float4 q4 = reinterpret_cast<const float4 *>(a.quats)[g];
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     Activated A;
-    bool ok = activate(ls, q, a.opacity_logits[g], A);
+    bool ok = activate(ls, q, a.opacity_logits[g], A) && live;
     float k[NC * 3];
     const float *cp = a.colors + (long long)g * NC * 3;
 #pragma unroll
@@ -164,6 +216,10 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
         const ViewInfo &vi = vb.v[v];
         long long r = (long long)v * a.n + g;
         int2 ext = make_int2(0, 0);
+        bool has = false;
+        CoverEllipse ell;
+        ell.u = ell.v = ell.A = ell.B = ell.C = ell.iA = ell.iC = ell.qc = 0.f;
+        int ctx0 = 0, cty0 = 0, cntx = 0, cnty = 0, cbin = 0;
         float T[12];
         load_pose(vi, a.Tdev, v, T);
         float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
@@ -230,22 +286,17 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                     a.rec[r] = R;
                     ext = make_int2(rx, ry);
                     mask |= 1u << v;
-                    const int bin = depth_bin(pz);
-                    for (int ty = ty0; ty <= ty1; ++ty) {
-                        const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
-                        for (int tx = tx0; tx <= tx1; ++tx) {
-                            const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
-                            if (tile_hit(u, vv, R.a.z, R.a.w, R.b.x, qc, px0, px1, py0, py1))
-                                atomicAdd(a.tile_count + (size_t)(vi.tile_base + ty * vi.tiles_x + tx) * kDepthBins + bin,
-                                          1u);
-                        }
-                    }
+                    has = true;
+                    ell = cover_ellipse(u, vv, R.a.z, R.a.w, R.b.x, qc);
+                    ctx0 = tx0; cty0 = ty0; cntx = tx1 - tx0 + 1; cnty = ty1 - ty0 + 1;
+                    cbin = depth_bin(pz);
                 }
             }
         }
-        a.ext[r] = ext;
+        count_cover_warp(a, vb, vi, has, ell, ctx0, cty0, cntx, cnty, cbin);
+        if (live) a.ext[r] = ext;
     }
-    a.vis_mask[g] = mask;
+    if (live) a.vis_mask[g] = mask;
 }
 
 // Backward of the projection for every view of one Gaussian, accumulating

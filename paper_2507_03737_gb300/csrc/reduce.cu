@@ -58,12 +58,12 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
     float acc[kGrad2d];
 #pragma unroll
     for (int q = 0; q < kGrad2d; ++q) acc[q] = 0.f;
-    const float C = a.rec[r].b.x, qc = a.rec[r].c.w;
+    const CoverEllipse ell = cover_ellipse(ra.x, ra.y, ra.z, ra.w, a.rec[r].b.x, a.rec[r].c.w);
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
             const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
             const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
-            if (!tile_hit(ra.x, ra.y, ra.z, ra.w, C, qc, px0, px1, py0, py1)) continue;  // not listed there
+            if (!tile_hit(ell, px0, px1, py0, py1)) continue;  // not listed there
             int t = vi.tile_base + ty * vi.tiles_x + tx;
             unsigned lo = a.tile_start[t * kDepthBins], hi = a.tile_start[(t + 1) * kDepthBins];
             while (lo < hi) {
@@ -83,13 +83,62 @@ constexpr int kLossThreads = 256;
 
 __device__ __forceinline__ float sgn(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
-__device__ __forceinline__ float l1_term(const float *x, const float *t, float *d, long long i, float c) {
-    float r = x[i] - t[i];
-    if (d) d[i] = c * sgn(r);
-    return c * fabsf(r);
+// One pixel-group of the L1 terms: W consecutive pixels of one view (W = 4 with
+// 16-byte vector loads when every plane is 16-byte aligned, else W = 1).
+template <int W>
+struct Lanes {
+    float x[W];
+};
+
+template <int W>
+__device__ __forceinline__ Lanes<W> ldv(const float *p) {
+    Lanes<W> r;
+    if (W == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        r.x[0] = q.x; r.x[1] = q.y; r.x[2] = q.z; r.x[3] = q.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) r.x[k] = p[k];
+    }
+    return r;
 }
 
-// grid.y = view; every thread handles whole pixels (all channels of each term).
+template <int W>
+__device__ __forceinline__ void stv(float *p, const Lanes<W> &v) {
+    if (W == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v.x[0], v.x[1], v.x[2], v.x[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) p[k] = v.x[k];
+    }
+}
+
+// L1 term over W pixels: adds sum c_k |x_k - t_k| to acc, writes c_k sign(x_k - t_k).
+template <int W>
+__device__ __forceinline__ void l1_group(const float *x, const float *t, float *d, long long i, const Lanes<W> &c,
+                                         float &acc) {
+    const Lanes<W> xv = ldv<W>(x + i), tv = ldv<W>(t + i);
+    Lanes<W> dv;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const float r = xv.x[k] - tv.x[k];
+        dv.x[k] = c.x[k] * sgn(r);
+        acc += c.x[k] * fabsf(r);
+    }
+    if (d) stv<W>(d + i, dv);
+}
+
+template <int W>
+__device__ __forceinline__ void zero_group(float *d, long long i) {
+    Lanes<W> z;
+#pragma unroll
+    for (int k = 0; k < W; ++k) z.x[k] = 0.f;
+    stv<W>(d + i, z);
+}
+
+// grid.y = view; every thread handles whole pixel groups (all channels of each
+// term), so each term's gradient is written by the thread that read its inputs.
+template <int W>
 __global__ void __launch_bounds__(kLossThreads) loss_kernel(const LossArgs a, const __grid_constant__ ViewBatch vb) {
     __shared__ float s[kLossThreads / 32];
     const int v = blockIdx.y;
@@ -97,20 +146,36 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const LossArgs a, co
     const long long HW = (long long)vi.w * vi.h;
     const long long p1 = vi.pix_base, p3 = 3 * vi.pix_base;
     const float P = (float)vb.total_pixels;
+    const float kr = a.w_rgb / (3.f * P), kd = a.w_depth / P, kg = a.w_geo / (3.f * P);
     float acc = 0.f;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += (long long)gridDim.x * blockDim.x) {
-        const float m = a.mask ? a.mask[p1 + p] : 1.f;
-        const float cr = m * a.w_rgb / (3.f * P), cd = m * a.w_depth / P, cg = m * a.w_geo / (3.f * P);
+    const long long groups = HW / W;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < groups;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long p = q * W;
+        Lanes<W> m;
+        if (a.mask) {
+            m = ldv<W>(a.mask + p1 + p);
+        } else {
+#pragma unroll
+            for (int k = 0; k < W; ++k) m.x[k] = 1.f;
+        }
+        Lanes<W> cr, cd, cg;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            cr.x[k] = m.x[k] * kr;
+            cd.x[k] = m.x[k] * kd;
+            cg.x[k] = m.x[k] * kg;
+        }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             const long long i = p3 + ch * HW + p;
-            if (a.t_rgb) acc += l1_term(a.rgb, a.t_rgb, a.d_rgb, i, cr);
-            else if (a.d_rgb) a.d_rgb[i] = 0.f;
-            if (a.t_pointmap) acc += l1_term(a.pointmap, a.t_pointmap, a.d_pointmap, i, cg);
-            else if (a.d_pointmap) a.d_pointmap[i] = 0.f;
+            if (a.t_rgb) l1_group<W>(a.rgb, a.t_rgb, a.d_rgb, i, cr, acc);
+            else if (a.d_rgb) zero_group<W>(a.d_rgb, i);
+            if (a.t_pointmap) l1_group<W>(a.pointmap, a.t_pointmap, a.d_pointmap, i, cg, acc);
+            else if (a.d_pointmap) zero_group<W>(a.d_pointmap, i);
         }
-        if (a.t_depth) acc += l1_term(a.depth, a.t_depth, a.d_depth, p1 + p, cd);
-        else if (a.d_depth) a.d_depth[p1 + p] = 0.f;
+        if (a.t_depth) l1_group<W>(a.depth, a.t_depth, a.d_depth, p1 + p, cd, acc);
+        else if (a.d_depth) zero_group<W>(a.d_depth, p1 + p);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -152,7 +217,15 @@ int loss_blocks_per_view() { return 64; }
 
 cudaError_t launch_loss(const LossArgs &a, const ViewBatch &vb, cudaStream_t s) {
     dim3 grid(loss_blocks_per_view(), vb.n_views);
-    loss_kernel<<<grid, kLossThreads, 0, s>>>(a, vb);
+    // 4-pixel vector groups when every plane of every view starts on a 16-byte boundary
+    bool vec = true;
+    for (int v = 0; v < vb.n_views; ++v)
+        vec = vec && ((long long)vb.v[v].w * vb.v[v].h) % 4 == 0 && vb.v[v].pix_base % 4 == 0;
+    const void *ptrs[] = {a.rgb, a.depth, a.pointmap, a.t_rgb, a.t_depth, a.t_pointmap, a.mask,
+                          a.d_rgb, a.d_depth, a.d_pointmap};
+    for (const void *q : ptrs) vec = vec && (reinterpret_cast<uintptr_t>(q) & 15u) == 0;
+    if (vec) loss_kernel<4><<<grid, kLossThreads, 0, s>>>(a, vb);
+    else loss_kernel<1><<<grid, kLossThreads, 0, s>>>(a, vb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     loss_final_kernel<<<1, 256, 0, s>>>(a.partial, loss_blocks_per_view() * vb.n_views, a.loss);

@@ -77,13 +77,14 @@ struct __align__(16) Record {
 // 3-sigma cutoff or the 1/255 skip -- widened for FP32 rounding of the conic
 // (relative 2e-5 plus 8e-7 times its condition number). The smallest q over
 // the box lies on its border unless the centre is inside; on each edge it is a
-// clamped one-dimensional minimum. Every operation is an explicit
-// round-to-nearest intrinsic, so the projection's counts, the emission and the
-// deterministic reduce take identical decisions (and the integer referee can
-// repeat them in plain C).
-__device__ __forceinline__ float edge_min_q(float a, float b, float c, float x, float lo, float hi) {
-    // min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0)
-    float y = __fdiv_rn(-__fmul_rn(b, x), c);
+// clamped one-dimensional minimum, whose stationary point uses the reciprocals
+// 1/A and 1/C (each a correctly rounded division, taken once per record). Every
+// operation is an explicit round-to-nearest intrinsic, so the projection's
+// counts, the emission and the deterministic reduce take identical decisions
+// (and the integer referee can repeat them in plain C).
+__device__ __forceinline__ float edge_min_q(float a, float b, float c, float ic, float x, float lo, float hi) {
+    // min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0, ic = 1 / c)
+    float y = __fmul_rn(-__fmul_rn(b, x), ic);
     y = fminf(fmaxf(y, lo), hi);
     const float t1 = __fmul_rn(a, __fmul_rn(x, x));
     const float t2 = __fmul_rn(__fmul_rn(2.0f, b), __fmul_rn(x, y));
@@ -91,16 +92,27 @@ __device__ __forceinline__ float edge_min_q(float a, float b, float c, float x, 
     return __fadd_rn(__fadd_rn(t1, t2), t3);
 }
 
-__device__ __forceinline__ bool tile_hit(float u, float v, float A, float B, float C, float qc, int px0, int px1,
-                                         int py0, int py1) {
-    const float dx0 = __fsub_rn((float)px0, u), dx1 = __fsub_rn((float)px1, u);
-    const float dy0 = __fsub_rn((float)py0, v), dy1 = __fsub_rn((float)py1, v);
-    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return qc >= 0.f;
-    float m = edge_min_q(A, B, C, dx0, dy0, dy1);
-    m = fminf(m, edge_min_q(A, B, C, dx1, dy0, dy1));
-    m = fminf(m, edge_min_q(C, B, A, dy0, dx0, dx1));
-    m = fminf(m, edge_min_q(C, B, A, dy1, dx0, dx1));
-    return m <= qc;
+struct CoverEllipse {
+    float u, v, A, B, C, iA, iC, qc;
+};
+
+__device__ __forceinline__ CoverEllipse cover_ellipse(float u, float v, float A, float B, float C, float qc) {
+    CoverEllipse e;
+    e.u = u; e.v = v; e.A = A; e.B = B; e.C = C; e.qc = qc;
+    e.iA = __fdiv_rn(1.0f, A);
+    e.iC = __fdiv_rn(1.0f, C);
+    return e;
+}
+
+__device__ __forceinline__ bool tile_hit(const CoverEllipse &e, int px0, int px1, int py0, int py1) {
+    const float dx0 = __fsub_rn((float)px0, e.u), dx1 = __fsub_rn((float)px1, e.u);
+    const float dy0 = __fsub_rn((float)py0, e.v), dy1 = __fsub_rn((float)py1, e.v);
+    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return e.qc >= 0.f;
+    float m = edge_min_q(e.A, e.B, e.C, e.iC, dx0, dy0, dy1);
+    m = fminf(m, edge_min_q(e.A, e.B, e.C, e.iC, dx1, dy0, dy1));
+    m = fminf(m, edge_min_q(e.C, e.B, e.A, e.iA, dy0, dx0, dx1));
+    m = fminf(m, edge_min_q(e.C, e.B, e.A, e.iA, dy1, dx0, dx1));
+    return m <= e.qc;
 }
 
 struct DevCounters {

@@ -2,8 +2,10 @@
 captured window-mapping iteration.
 
 Tolerances: the step is elementwise FP32 (one division of the bias-corrected
-moments, one square root): moments within 1e-5 relative (the first moment, a
-sum of terms of either sign, within 1e-5 of its largest entry), parameters within
+moments, one square root): moments within 1e-5 relative or 1e-5 of the
+tensor's largest entry (the first moment sums terms of either sign, and the
+log-scale gradient adds an L_iso term that can cancel the input gradient),
+parameters within
 1e-6 absolute plus 1e-6 relative after four steps (parameters are O(1), steps
 O(lr)). The L_iso sign decisions are FP32 on the GPU; the inputs keep every
 scale at least 1e-4 (relative) from its Gaussian's mean scale, where FP32 and
@@ -81,7 +83,10 @@ def test_map_adam_step_matches_oracle(R, sh, missing):
             # m = beta1 m + (1 - beta1) g can cancel: its error scales with the terms, not the result
             np.testing.assert_allclose(m[k].cpu().numpy(), ref_s[k][0], rtol=1e-5,
                                        atol=1e-5 * float(np.abs(ref_s[k][0]).max()), err_msg=k)
-            np.testing.assert_allclose(v[k].cpu().numpy(), ref_s[k][1], rtol=1e-5, atol=1e-18, err_msg=k)
+            # the log-scale gradient adds the L_iso term, which can cancel the input gradient:
+            # both moments are checked against the scale of their largest entry as well
+            np.testing.assert_allclose(v[k].cpu().numpy(), ref_s[k][1], rtol=1e-5,
+                                       atol=1e-5 * float(np.abs(ref_s[k][1]).max()), err_msg=k)
     assert int(step[0]) == 4
 
 
