@@ -305,6 +305,20 @@ class Workload:
                               g["quats"], g["opacity_logits"], g["colors"], g["twist"][v:v + 1], int(v > 0))
 
 
+def whole_job_rate(total_ms, steps, views_per_rank, world, device):
+    """Replicas-only scaling: every rank renders its own copy of the window, so the
+    job's time is the slowest rank's and its rate counts the views of all ranks.
+    Returns (ms per step, views/s of the whole job)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * views_per_rank / (ms_per_step / 1e3)
+
+
 def timed(fn, steps, flush, stream_sync=True):
     import torch
     times = []
@@ -426,13 +440,7 @@ def run_native(args):
                 stage_tot[k] = stage_tot.get(k, 0.0) + v
     B.s3gs_set_timing(R.ctx, 0)
     st, K, cap = B.s3gs_state_check(R.ctx, R.state)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * wl.V / (ms_per_step / 1e3)
+    ms_per_step, value = whole_job_rate(sum(step_ms), args.steps, wl.V, world, device)
     stages = {k: v / args.steps for k, v in stage_tot.items()}
 
     # ---- per-view path (eager) for the comparison the metric names
