@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--bppt", type=int, default=0, help="pixels per backward-blend thread (0 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--deterministic", type=int, default=0)
-    ap.add_argument("--recompute", type=int, default=0)
+    ap.add_argument("--recompute", type=int, default=-1, help="1 = recompute the blend state in the backward "
+                    "(default: on for config 5 only)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,6 +63,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="--row pose: use the library's default schedule instead of autotuning it for the "
                          "single-view workload first")
+    ap.add_argument("--autotune", type=int, default=-1,
+                    help="window row: 1 = autotune the blend schedule for the workload before timing (default: "
+                         "on for the single-view config 2 and the uneven-resolution config 4)")
     return ap.parse_args()
 
 
@@ -188,7 +192,9 @@ def workload_config(sc, args, extra=None):
            "loss": f"L1 rgb {W_RGB} + depth {W_DEPTH} + pointmap {W_GEO} (Eq. 17)",
            "tile": args.tile, "batch": args.batch or 256, "pixels_per_thread": [args.ppt or 2, args.bppt or 4],
            "blocks_per_sm": args.blocks_per_sm,
-           "deterministic": args.deterministic, "recompute": args.recompute,
+           "deterministic": args.deterministic, "recompute": int(args.recompute if args.recompute >= 0
+                                                                  else args.config == 5),
+           "backward": "pose-only (d_twist)" if args.config == 4 else "all parameters + twists",
            "l2": "flushed between timed steps (256 MB write outside the step events)"}
     if extra:
         cfg.update(extra)
@@ -237,14 +243,17 @@ class Workload:
         self.cams = sc.cameras
         self.V = len(self.cams)
         tw, th = tile_shape(args.tile)
+        # config 5 runs with recomputed blend state, as its workload specifies
+        recompute = args.recompute if args.recompute >= 0 else int(args.config == 5)
         self.opt = B.s3gs_options_default(tile_w=tw, tile_h=th, blocks_per_sm=args.blocks_per_sm,
-                                          deterministic=args.deterministic, recompute=args.recompute)
+                                          deterministic=args.deterministic, recompute=recompute)
         if args.batch:
             self.opt.batch = args.batch
         if args.ppt:
             self.opt.pixels_per_thread = args.ppt
         if args.bppt:
             self.opt.bwd_pixels_per_thread = args.bppt
+        self.pose_only = args.config == 4
         self.R = Renderer(device.index or 0, self.opt)
         self.p = self.R.upload(sc)
         P = sum(c["width"] * c["height"] for c in self.cams)
@@ -281,8 +290,12 @@ class Workload:
                             self.tgt["rgb"], self.tgt["depth"], self.tgt["pointmap"], None, W_RGB, W_DEPTH, W_GEO,
                             self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], self.loss)
         g = self.grads
-        B.s3gs_render_bwd(R.ctx, R.state, self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], None,
-                          g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["colors"], g["twist"], 0)
+        if self.pose_only:  # tracking-style backward: only the view twists (config 4)
+            B.s3gs_render_bwd(R.ctx, R.state, self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], None,
+                              None, None, None, None, None, g["twist"], 0)
+        else:
+            B.s3gs_render_bwd(R.ctx, R.state, self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], None,
+                              g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["colors"], g["twist"], 0)
 
     def step_per_view(self):
         """The same step, one view per launch sequence (gradients accumulated)."""
@@ -301,8 +314,11 @@ class Workload:
             B.s3gs_mapping_loss(R.ctx, self.view_cams[v], 1, o["rgb"], o["depth"], o["pointmap"], t["rgb"], t["depth"],
                                 t["pointmap"], None, W_RGB, W_DEPTH, W_GEO, d["rgb"], d["depth"], d["pointmap"],
                                 self.loss)
-            B.s3gs_render_bwd(R.ctx, R.state, d["rgb"], d["depth"], d["pointmap"], None, g["means"], g["log_scales"],
-                              g["quats"], g["opacity_logits"], g["colors"], g["twist"][v:v + 1], int(v > 0))
+            pg = {k: (None if self.pose_only else g[k]) for k in ("means", "log_scales", "quats", "opacity_logits",
+                                                                    "colors")}
+            B.s3gs_render_bwd(R.ctx, R.state, d["rgb"], d["depth"], d["pointmap"], None, pg["means"],
+                              pg["log_scales"], pg["quats"], pg["opacity_logits"], pg["colors"], g["twist"][v:v + 1],
+                              int(v > 0))
 
 
 def whole_job_rate(total_ms, steps, views_per_rank, world, device):
@@ -357,6 +373,13 @@ def run_native(args):
     R = wl.R
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > 129 MB L2
     flush = lambda: flush_buf.zero_()
+    tuned = None
+    if (args.autotune if args.autotune >= 0 else int(args.config in (2, 4))) == 1:
+        from paper_2507_03737_gb300.autotune import autotune, options_to_dict
+        best = autotune(R, wl.p, wl.cams, base=wl.opt, repeats=3, rounds=2)
+        for k, v in options_to_dict(best).items():
+            setattr(wl.opt, k, v)
+        tuned = options_to_dict(best)
 
     # size every buffer (auto-grow), then switch to the no-sync capture-safe mode
     wl.step_batched()
@@ -475,7 +498,8 @@ def run_native(args):
     if not args.no_e2e:
         pk = ("means", "log_scales", "quats", "opacity_logits", "colors")
         host_in = {k: wl.p[k].cpu().pin_memory() for k in pk}
-        host_out = {k: torch.empty(wl.grads[k].shape, dtype=torch.float32).pin_memory() for k in wl.grads}
+        outs = ("twist",) if wl.pose_only else tuple(wl.grads)
+        host_out = {k: torch.empty(wl.grads[k].shape, dtype=torch.float32).pin_memory() for k in outs}
         host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
         h2d = sum(v.numel() * 4 for v in host_in.values())
         d2h = sum(v.numel() * 4 for v in host_out.values()) + 4
@@ -546,7 +570,12 @@ def run_native(args):
         line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded config generator; no dataset)",
-                "config": workload_config(sc, args, {"graph": use_graph, "duplicates": K}),
+                "config": workload_config(sc, args, {"graph": use_graph, "duplicates": K, "autotuned": tuned,
+                                                     "tile": f"{wl.opt.tile_w}x{wl.opt.tile_h}",
+                                                     "pixels_per_thread": [int(wl.opt.pixels_per_thread),
+                                                                           int(wl.opt.bwd_pixels_per_thread)],
+                                                     "batch": int(wl.opt.batch),
+                                                     "blocks_per_sm": int(wl.opt.blocks_per_sm)}),
                 "per_view": per_view, "stages_ms": stages, "stages_timed_in": stage_src,
                 "pairs": {"fwd_processed": fwd_proc, "fwd_blended": fwd_blend, "bwd_processed": bwd_proc,
                           "pairs_per_s_fwd_bwd": (fwd_proc + bwd_proc) * world / (ms_per_step / 1e3),
@@ -737,7 +766,7 @@ def run_pose(args):
     torch.cuda.set_device(local)
     tw, th = tile_shape(args.tile)
     opt = B.s3gs_options_default(tile_w=tw, tile_h=th, blocks_per_sm=args.blocks_per_sm,
-                                 deterministic=args.deterministic, recompute=args.recompute)
+                                 deterministic=args.deterministic, recompute=max(args.recompute, 0))
     for k, a in (("batch", args.batch), ("pixels_per_thread", args.ppt), ("bwd_pixels_per_thread", args.bppt)):
         if a:
             setattr(opt, k, a)

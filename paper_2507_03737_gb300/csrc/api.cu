@@ -548,6 +548,10 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
     ba.batch = st->opt.batch;
     ba.ppt = st->opt.bwd_pixels_per_thread;
     ba.counting = ctx->counting;
+    // Colour and opacity gradients feed only d_colors and d_opacity_logits, and (for
+    // SH degree >= 1) the twist through the view direction; without them the blend
+    // accumulates only the geometry slots.
+    ba.geom_only = !det && !d_colors && !d_opacity_logits && st->g.sh_degree == 0;
     const long long T = vb.total_tiles;
     long long grid = persistent ? std::min<long long>(T, (long long)ctx->num_sms * st->opt.blocks_per_sm) : T;
     {

@@ -111,6 +111,36 @@ __device__ __forceinline__ int warp_reduce_scatter10(const float v[kGrad2d], flo
     return slot + (b4 ? 5 : 0);
 }
 
+// The same for the six geometry slots (u, v, A, B, C, z) of a geometry-only
+// backward: 3 + 2 + 1 shuffles halve the lanes' values, two more finish the sums;
+// lanes with lane & 3 == 0 own one slot each (compact index 0..5, or -1).
+__device__ __forceinline__ int warp_reduce_scatter6(const float v[6], float *sum) {
+    const unsigned lane = threadIdx.x & 31u;
+    const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u;
+    float a3[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float send = b4 ? v[i] : v[i + 3];
+        const float keep = b4 ? v[i + 3] : v[i];
+        a3[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float c2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float hi = j == 0 ? a3[2] : 0.f;
+        const float send = b3 ? a3[j] : hi;
+        const float keep = b3 ? hi : a3[j];
+        c2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float e = (b2 ? c2[1] : c2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? c2[0] : c2[1], 4);
+    e += __shfl_xor_sync(0xffffffffu, e, 2);
+    e += __shfl_xor_sync(0xffffffffu, e, 1);
+    *sum = e;
+    const int slot = b3 ? (b2 ? -1 : 2) : (b2 ? 1 : 0);
+    if ((lane & 3u) || slot < 0) return -1;
+    return slot + (b4 ? 3 : 0);
+}
+
 template <int TW, int TH, int P, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a, const __grid_constant__ ViewBatch vb) {
     constexpr int NT = TW * TH / P;
@@ -204,7 +234,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
     }
 }
 
-template <int TW, int TH, int P, bool RECOMPUTE, bool DET, bool COUNT>
+template <int TW, int TH, int P, bool RECOMPUTE, bool DET, bool COUNT, bool GEOM = false>
 __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a, const __grid_constant__ ViewBatch vb) {
     constexpr int NT = TW * TH / P;
     constexpr int NW = NT / 32;
@@ -360,9 +390,11 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                     const float da = __fmul_rn(Tk, __fsub_rn(f, Bacc[p]));
                     Bacc[p] = __fmaf_rn(f, al, __fmul_rn(om, Bacc[p]));
                     T[p] = Tk;
-                    vals[kGR] = __fmaf_rn(w, gC0[p], vals[kGR]);
-                    vals[kGG] = __fmaf_rn(w, gC1[p], vals[kGG]);
-                    vals[kGBl] = __fmaf_rn(w, gC2[p], vals[kGBl]);
+                    if (!GEOM) {
+                        vals[kGR] = __fmaf_rn(w, gC0[p], vals[kGR]);
+                        vals[kGG] = __fmaf_rn(w, gC1[p], vals[kGG]);
+                        vals[kGBl] = __fmaf_rn(w, gC2[p], vals[kGBl]);
+                    }
                     vals[kGZ] = __fmaf_rn(w, gD[p], vals[kGZ]);
                     if (!pe.clamped) {
                         // alpha = 2^(p + log2 o): d alpha / d logit = alpha (1 - o),
@@ -370,7 +402,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                         const float g = __fmul_rn(da, al);
                         const float ngl = __fmul_rn(-kLn2, g);
                         const float hg = __fmul_rn(-0.5f, g);
-                        vals[kGO] = __fmaf_rn(g, __fsub_rn(1.f, q1.z), vals[kGO]);
+                        if (!GEOM) vals[kGO] = __fmaf_rn(g, __fsub_rn(1.f, q1.z), vals[kGO]);
                         vals[kGA] = __fmaf_rn(__fmul_rn(hg, pe.dx), pe.dx, vals[kGA]);
                         vals[kGB] = __fmaf_rn(__fmul_rn(-g, pe.dx), pe.dy, vals[kGB]);
                         vals[kGC] = __fmaf_rn(__fmul_rn(hg, pe.dy), pe.dy, vals[kGC]);
@@ -384,6 +416,13 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                     float sum;
                     const int slot = warp_reduce_scatter10(vals, &sum);
                     if (slot >= 0) s_part[((size_t)warp * B + k) * kGrad2d + slot] = sum;
+                } else if (GEOM) {
+                    if (__any_sync(0xffffffffu, contrib)) {
+                        const float gv[6] = {vals[kGU], vals[kGV], vals[kGA], vals[kGB], vals[kGC], vals[kGZ]};
+                        float sum;
+                        const int c = warp_reduce_scatter6(gv, &sum);
+                        if (c >= 0) atomicAdd(a.grad2d + (rbase + s_g[k]) * kGrad2d + (c == 5 ? kGZ : c), sum);
+                    }
                 } else if (__any_sync(0xffffffffu, contrib)) {
                     float sum;
                     const int slot = warp_reduce_scatter10(vals, &sum);
@@ -441,11 +480,11 @@ cudaError_t fwd_impl2(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStr
     return a.counting ? fwd_impl3<TW, TH, P, true>(a, vb, grid, s) : fwd_impl3<TW, TH, P, false>(a, vb, grid, s);
 }
 
-template <int TW, int TH, int P, bool R, bool D, bool C>
+template <int TW, int TH, int P, bool R, bool D, bool C, bool G = false>
 cudaError_t bwd_impl4(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
     static int cached = 0;
     const size_t sm = bwd_smem(a.batch, TW * TH / P / 32, D);
-    auto k = blend_bwd_kernel<TW, TH, P, R, D, C>;
+    auto k = blend_bwd_kernel<TW, TH, P, R, D, C, G>;
     cudaError_t e = ensure_smem(k, sm, &cached);
     if (e != cudaSuccess) return e;
     k<<<grid, TW * TH / P, sm, s>>>(a, vb);
@@ -454,8 +493,10 @@ cudaError_t bwd_impl4(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStr
 
 template <int TW, int TH, int P, bool R, bool D>
 cudaError_t bwd_impl3(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    return a.counting ? bwd_impl4<TW, TH, P, R, D, true>(a, vb, grid, s)
-                      : bwd_impl4<TW, TH, P, R, D, false>(a, vb, grid, s);
+    if (a.counting) return bwd_impl4<TW, TH, P, R, D, true>(a, vb, grid, s);
+    if constexpr (!D)
+        if (a.geom_only) return bwd_impl4<TW, TH, P, R, D, false, true>(a, vb, grid, s);
+    return bwd_impl4<TW, TH, P, R, D, false>(a, vb, grid, s);
 }
 
 template <int TW, int TH, int P>

@@ -281,6 +281,7 @@ struct BlendArgs {
     int batch;
     int ppt;            // pixels per thread (1, 2 or 4)
     int counting;
+    int geom_only;      // backward: only the geometry slots (u, v, conic, z) are needed
 };
 cudaError_t launch_blend_fwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
 cudaError_t launch_blend_bwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);

@@ -396,3 +396,22 @@ def test_guard_cone_matches_oracle(R):
                 assert rel_l2(g_gpu[k], g_ref[k]) < 1e-3, (g, k)
     finally:
         O.set_guard(1.5)
+
+
+def test_pose_only_backward_matches_the_full_twist(R):
+    """A backward asking only for the twist (degree-0 colour) accumulates only the
+    geometry slots; its twist equals the full backward's up to summation order."""
+    sc = scenes.config_scene(1)
+    sc2 = scenes.tiny_scene(4, n=200, width=64, height=48, n_views=3)
+    for s in (sc, sc2):
+        R.render_np(s)
+        V = len(s.cameras)
+        P = sum(c["width"] * c["height"] for c in s.cameras)
+        rng = np.random.default_rng(3)
+        ups = dict(d_rgb=rng.standard_normal(3 * P), d_depth=rng.standard_normal(P),
+                   d_pointmap=rng.standard_normal(3 * P), d_alpha=rng.standard_normal(P))
+        full = R.backward_np(ups, V)
+        pose = R.backward_np(ups, V, want=("twist",))
+        assert set(pose) == {"twist"}
+        np.testing.assert_allclose(pose["twist"], full["twist"], rtol=1e-5,
+                                   atol=1e-6 * float(np.abs(full["twist"]).max()))
