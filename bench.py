@@ -528,7 +528,9 @@ def run_native(args):
     #   forward, each blended pair: transmittance, weight, 4 accumulations  10
     #   backward, each contributing pair: T restore, weight, dalpha, behind
     #   value, 10 gradient terms and their 10 accumulations                51
-    flops = {"blend_fwd": 13 * fwd_proc + 10 * fwd_blend, "blend_bwd": 13 * bwd_proc + 51 * fwd_blend}
+    #   (a pose-only backward skips the colour and opacity terms: 37 instead of 51)
+    flops = {"blend_fwd": 13 * fwd_proc + 10 * fwd_blend,
+             "blend_bwd": 13 * bwd_proc + (37 if wl.pose_only else 51) * fwd_blend}
     n_rec = sc.n * wl.V
     nc = (sc.sh_degree + 1) ** 2
     p_in = 4 * (3 + 3 + 4 + 1 + 3 * nc)
@@ -827,8 +829,27 @@ def run_pose(args):
         roof = {"kernel": "project", "bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": ach / float(peaks["hbm_gbs"]), "traffic": None, "ms_per_launch": stages[dominant],
                 "peak_of": peak_src}
+    elif dominant in ("blend_fwd", "blend_bwd"):
+        # pair counts of one iteration (counting mode, outside the timed region); the
+        # pose-only backward accumulates the geometry slots only: 13 flops per
+        # evaluated pair + 37 per contributing pair (the 51 of the full backward
+        # minus the colour and opacity terms)
+        B.s3gs_set_counting(R.ctx, 1)
+        pr.iteration()
+        cnt = B.s3gs_read_counters(R.ctx, R.state)
+        B.s3gs_set_counting(R.ctx, 0)
+        flops = {"blend_fwd": 13 * cnt["fwd_processed"] + 10 * cnt["fwd_blended"],
+                 "blend_bwd": 13 * cnt["bwd_processed"] + 37 * cnt["fwd_blended"]}
+        sm_count = torch.cuda.get_device_properties(R.device).multi_processor_count
+        clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = sm_count * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+        ach = flops[dominant] / (stages[dominant] / 1e3) / 1e12
+        roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "ms_per_launch": stages[dominant],
+                "flops_per_launch": flops[dominant], "pairs": cnt,
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz", "peak_of": peak_src}
     elif dominant is not None:
-        roof = {"kernel": dominant, "bound": "see the window row", "ms_per_launch": stages[dominant]}
+        roof = {"kernel": dominant, "bound": "unclassified", "ms_per_launch": stages[dominant]}
     cpu = None
     if not args.no_cpu_baseline:
         dt, ips, cores, crop = pose_oracle_sample(sc, true_cam, start_cam)
