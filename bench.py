@@ -286,16 +286,14 @@ class Workload:
                                                            self.p["sh_degree"]),
                           self.cam_arr, self.V, None, self.opt, self.out["rgb"], self.out["depth"],
                           self.out["pointmap"], self.out["alpha"])
-        B.s3gs_mapping_loss(R.ctx, self.cam_arr, self.V, self.out["rgb"], self.out["depth"], self.out["pointmap"],
-                            self.tgt["rgb"], self.tgt["depth"], self.tgt["pointmap"], None, W_RGB, W_DEPTH, W_GEO,
-                            self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], self.loss)
+        # the L1 mapping loss fused into the backward (one pass, no gradient images)
         g = self.grads
-        if self.pose_only:  # tracking-style backward: only the view twists (config 4)
-            B.s3gs_render_bwd(R.ctx, R.state, self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], None,
-                              None, None, None, None, None, g["twist"], 0)
-        else:
-            B.s3gs_render_bwd(R.ctx, R.state, self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], None,
-                              g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["colors"], g["twist"], 0)
+        o, t = self.out, self.tgt
+        pg = {k: (None if self.pose_only else g[k]) for k in ("means", "log_scales", "quats", "opacity_logits",
+                                                             "colors")}
+        B.s3gs_render_bwd_l1(R.ctx, R.state, o["rgb"], o["depth"], o["pointmap"], t["rgb"], t["depth"], t["pointmap"],
+                             None, W_RGB, W_DEPTH, W_GEO, self.loss, pg["means"], pg["log_scales"], pg["quats"],
+                             pg["opacity_logits"], pg["colors"], g["twist"], 0)
 
     def step_per_view(self):
         """The same step, one view per launch sequence (gradients accumulated)."""
@@ -307,18 +305,14 @@ class Workload:
             sl1 = slice(off, off + hw)
             sl3 = slice(3 * off, 3 * (off + hw))
             o = {k: (self.out[k][sl3] if k in ("rgb", "pointmap") else self.out[k][sl1]) for k in self.out}
-            d = {k: (self.dout[k][sl3] if k in ("rgb", "pointmap") else self.dout[k][sl1]) for k in self.dout}
             t = {k: (self.tgt[k][sl3] if k in ("rgb", "pointmap") else self.tgt[k][sl1]) for k in self.tgt}
             B.s3gs_render_fwd(R.ctx, R.state, gs, self.view_cams[v], 1, None, self.opt, o["rgb"], o["depth"],
                               o["pointmap"], o["alpha"])
-            B.s3gs_mapping_loss(R.ctx, self.view_cams[v], 1, o["rgb"], o["depth"], o["pointmap"], t["rgb"], t["depth"],
-                                t["pointmap"], None, W_RGB, W_DEPTH, W_GEO, d["rgb"], d["depth"], d["pointmap"],
-                                self.loss)
             pg = {k: (None if self.pose_only else g[k]) for k in ("means", "log_scales", "quats", "opacity_logits",
                                                                     "colors")}
-            B.s3gs_render_bwd(R.ctx, R.state, d["rgb"], d["depth"], d["pointmap"], None, pg["means"],
-                              pg["log_scales"], pg["quats"], pg["opacity_logits"], pg["colors"], g["twist"][v:v + 1],
-                              int(v > 0))
+            B.s3gs_render_bwd_l1(R.ctx, R.state, o["rgb"], o["depth"], o["pointmap"], t["rgb"], t["depth"],
+                                 t["pointmap"], None, W_RGB, W_DEPTH, W_GEO, self.loss, pg["means"], pg["log_scales"],
+                                 pg["quats"], pg["opacity_logits"], pg["colors"], g["twist"][v:v + 1], int(v > 0))
 
 
 def whole_job_rate(total_ms, steps, views_per_rank, world, device):

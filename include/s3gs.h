@@ -174,6 +174,24 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *state, const float *d_rgb
                             float *d_opacity_logits, float *d_colors, float *d_twist,
                             int32_t accumulate, void *stream);
 
+/* Backward with the L1 mapping loss of s3gs_mapping_loss fused in (Eq. 10/15/17):
+ * the same result as s3gs_mapping_loss on the forward's outputs followed by
+ * s3gs_render_bwd with the gradients it writes (and d_alpha = NULL), in one pass
+ * that forms each pixel's upstream gradient from its output and target instead
+ * of writing and re-reading gradient images. rgb, depth, pointmap: the outputs
+ * the last forward on `state` wrote (device, packed); t_rgb, t_depth,
+ * t_pointmap: targets (NULL = term off); mask: per-pixel weights (NULL = 1);
+ * w_*: term weights; loss_device: device float [1] out, the loss value (the
+ * same terms as s3gs_mapping_loss, summed in another order; NULL = not wanted).
+ * Gradient outputs, accumulate and errors as in s3gs_render_bwd; INVALID also
+ * for a target without its output. */
+s3gs_status s3gs_render_bwd_l1(s3gs_ctx *ctx, s3gs_state *state, const float *rgb, const float *depth,
+                               const float *pointmap, const float *t_rgb, const float *t_depth,
+                               const float *t_pointmap, const float *mask, float w_rgb, float w_depth, float w_geo,
+                               float *loss_device, float *d_means, float *d_log_scales, float *d_quats,
+                               float *d_opacity_logits, float *d_colors, float *d_twist, int32_t accumulate,
+                               void *stream);
+
 /* Synchronise with the state's last stream and report its device-side status:
  * S3GS_E_CAPACITY if the last forward overflowed. *n_duplicates (optional)
  * receives that forward's number of (Gaussian, tile) pairs, *capacity

@@ -19,7 +19,7 @@ __all__ = [
     "S3GS_E_NOMEM", "S3GS_E_STATE", "S3GS_MAX_VIEWS", "S3GSError", "Gaussians", "Camera",
     "Options", "lib", "s3gs_options_default", "s3gs_create", "s3gs_destroy", "s3gs_last_error",
     "s3gs_state_create", "s3gs_state_destroy", "s3gs_reserve", "s3gs_render_fwd",
-    "s3gs_render_bwd", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_debug_records",
+    "s3gs_render_bwd", "s3gs_render_bwd_l1", "s3gs_state_check", "s3gs_mapping_loss", "s3gs_debug_records",
     "s3gs_debug_binning", "s3gs_debug_cover", "s3gs_set_counting", "s3gs_read_counters", "s3gs_version",
     "s3gs_set_timing", "s3gs_read_timing", "STAGES", "s3gs_mapping_loss_noalloc",
     "make_cameras", "make_gaussians", "check", "AlignParams", "s3gs_align_params_default",
@@ -108,6 +108,8 @@ def _load():
                                            ctypes.c_int32, _P, ctypes.POINTER(Options), _P, _P, _P, _P, _P]),
         "s3gs_render_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                            ctypes.c_int32, _P]),
+        "s3gs_render_bwd_l1": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float,
+                                              ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
         "s3gs_state_check": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int64)]),
         "s3gs_mapping_loss": (ctypes.c_int, [_P, ctypes.POINTER(Camera), ctypes.c_int32, _P, _P, _P, _P, _P,
@@ -270,6 +272,16 @@ def s3gs_render_bwd(ctx, state, d_rgb, d_depth, d_pointmap, d_alpha, d_means, d_
                                      _ptr(d_alpha), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats),
                                      _ptr(d_opacity_logits), _ptr(d_colors), _ptr(d_twist),
                                      int(accumulate), _stream(stream)))
+
+
+def s3gs_render_bwd_l1(ctx, state, rgb, depth, pointmap, t_rgb, t_depth, t_pointmap, mask, w_rgb, w_depth, w_geo,
+                       loss_device, d_means, d_log_scales, d_quats, d_opacity_logits, d_colors, d_twist, accumulate=0,
+                       stream=None):
+    check(ctx, lib().s3gs_render_bwd_l1(ctx, state, _ptr(rgb), _ptr(depth), _ptr(pointmap), _ptr(t_rgb),
+                                        _ptr(t_depth), _ptr(t_pointmap), _ptr(mask), float(w_rgb), float(w_depth),
+                                        float(w_geo), _ptr(loss_device), _ptr(d_means), _ptr(d_log_scales),
+                                        _ptr(d_quats), _ptr(d_opacity_logits), _ptr(d_colors), _ptr(d_twist),
+                                        int(accumulate), _stream(stream)))
 
 
 def s3gs_state_check(ctx, state, raise_on_error=True):

@@ -75,6 +75,7 @@ struct s3gs_state {
     DevBuf<float> T_final;
     DevBuf<unsigned> n_last;
     DevBuf<float> twist_part;
+    DevBuf<float> loss_part;  // fused-loss backward: one partial per blend CTA
     unsigned *bucket = nullptr;
     DevCounters *ctr = nullptr;
     DevCounters *ctr_host = nullptr;  // pinned
@@ -235,8 +236,20 @@ s3gs_status ensure_forward_buffers(s3gs_ctx *ctx, s3gs_state *st, long long n_re
     }
     long long need_twp = (long long)project_bwd_grid(n > 0 ? n : 1) * n_views * 6;
     if ((r = grow(ctx, st->twist_part, need_twp, s, "twist_partials")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->loss_part, n_tiles + 1, s, "loss_partials")) != S3GS_OK) return r;
     return S3GS_OK;
 }
+
+// Inputs of the backward with the L1 mapping loss fused in.
+struct L1Fused {
+    const float *rgb, *depth, *pointmap, *t_rgb, *t_depth, *t_pointmap, *mask;
+    float w_rgb, w_depth, w_geo;
+};
+
+s3gs_status render_bwd_impl(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, const float *d_depth,
+                            const float *d_pointmap, const float *d_alpha, const L1Fused *l1, float *loss_device,
+                            float *d_means, float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                            float *d_colors, float *d_twist, int32_t accumulate, void *stream_);
 
 }  // namespace
 
@@ -348,7 +361,7 @@ void s3gs_state_destroy(s3gs_state *st) {
     cudaDeviceSynchronize();
     void *bufs[] = {st->rec.p, st->ext.p, st->vis_mask.p, st->grad2d.p, st->tile_count.p, st->tile_start.p, st->cursor.p,
                     st->order.p, st->scan_part.p, st->bucket, st->keys.p, st->det_partial.p, st->T_final.p,
-                    st->n_last.p, st->twist_part.p, st->ctr};
+                    st->n_last.p, st->twist_part.p, st->loss_part.p, st->ctr};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (st->ctr_host) cudaFreeHost(st->ctr_host);
@@ -514,6 +527,35 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
                             const float *d_pointmap, const float *d_alpha, float *d_means, float *d_log_scales,
                             float *d_quats, float *d_opacity_logits, float *d_colors, float *d_twist,
                             int32_t accumulate, void *stream_) {
+    return render_bwd_impl(ctx, st, d_rgb, d_depth, d_pointmap, d_alpha, nullptr, nullptr, d_means, d_log_scales,
+                           d_quats, d_opacity_logits, d_colors, d_twist, accumulate, stream_);
+}
+
+s3gs_status s3gs_render_bwd_l1(s3gs_ctx *ctx, s3gs_state *st, const float *rgb, const float *depth,
+                               const float *pointmap, const float *t_rgb, const float *t_depth,
+                               const float *t_pointmap, const float *mask, float w_rgb, float w_depth, float w_geo,
+                               float *loss_device, float *d_means, float *d_log_scales, float *d_quats,
+                               float *d_opacity_logits, float *d_colors, float *d_twist, int32_t accumulate,
+                               void *stream_) {
+    if (!ctx) return S3GS_E_INVALID;
+    if ((t_rgb && !rgb) || (t_depth && !depth) || (t_pointmap && !pointmap))
+        return fail(ctx, S3GS_E_INVALID, "render_bwd_l1: a target is given without its rendered output");
+    L1Fused l1;
+    l1.rgb = rgb; l1.depth = depth; l1.pointmap = pointmap;
+    l1.t_rgb = t_rgb; l1.t_depth = t_depth; l1.t_pointmap = t_pointmap; l1.mask = mask;
+    l1.w_rgb = w_rgb; l1.w_depth = w_depth; l1.w_geo = w_geo;
+    return render_bwd_impl(ctx, st, nullptr, nullptr, nullptr, nullptr, &l1, loss_device, d_means, d_log_scales,
+                           d_quats, d_opacity_logits, d_colors, d_twist, accumulate, stream_);
+}
+
+}  // extern "C"
+
+namespace {
+
+s3gs_status render_bwd_impl(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, const float *d_depth,
+                            const float *d_pointmap, const float *d_alpha, const L1Fused *l1, float *loss_device,
+                            float *d_means, float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                            float *d_colors, float *d_twist, int32_t accumulate, void *stream_) {
     if (!ctx) return S3GS_E_INVALID;
     if (!st) return fail(ctx, S3GS_E_INVALID, "render_bwd: null state");
     if (!st->valid) return fail(ctx, S3GS_E_STATE, "render_bwd: no successful forward on this state");
@@ -552,11 +594,23 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
     // SH degree >= 1) the twist through the view direction; without them the blend
     // accumulates only the geometry slots.
     ba.geom_only = !det && !d_colors && !d_opacity_logits && st->g.sh_degree == 0;
+    if (l1) {
+        const float Ptot = (float)vb.total_pixels;
+        ba.l1 = 1;
+        ba.o_rgb = l1->rgb; ba.o_depth = l1->depth; ba.o_pointmap = l1->pointmap;
+        ba.t_rgb = l1->t_rgb; ba.t_depth = l1->t_depth; ba.t_pointmap = l1->t_pointmap; ba.mask = l1->mask;
+        ba.kr = l1->w_rgb / (3.f * Ptot); ba.kd = l1->w_depth / Ptot; ba.kg = l1->w_geo / (3.f * Ptot);
+        ba.loss_partial = st->loss_part.p;
+    }
     const long long T = vb.total_tiles;
     long long grid = persistent ? std::min<long long>(T, (long long)ctx->num_sms * st->opt.blocks_per_sm) : T;
     {
         StageTimer tm(ctx, kStBlendBwd, s);
         CK(launch_blend_bwd(ba, vb, (int)grid, s), "blend_bwd");
+    }
+    if (l1 && loss_device) {
+        StageTimer tm(ctx, kStLoss, s);
+        CK(launch_loss_final(st->loss_part.p, (int)grid, loss_device, s), "loss_final");
     }
 
     if (det) {
@@ -597,6 +651,10 @@ s3gs_status s3gs_render_bwd(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
     st->stream = s;
     return S3GS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 s3gs_status s3gs_state_check(s3gs_ctx *ctx, s3gs_state *st, int64_t *n_duplicates, int64_t *capacity) {
     if (!ctx || !st) return fail(ctx, S3GS_E_INVALID, "state_check: null argument");

@@ -234,6 +234,8 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
     }
 }
 
+__device__ __forceinline__ float l1_sign(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
 template <int TW, int TH, int P, bool RECOMPUTE, bool DET, bool COUNT, bool GEOM = false>
 __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a, const __grid_constant__ ViewBatch vb) {
     constexpr int NT = TW * TH / P;
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (a.ctr->overflow) return;
     unsigned long long n_proc = 0;
+    float loss_acc = 0.f;  // fused L1 loss of this thread's pixels
     for (int iter = 0;; ++iter) {
         const int t = next_tile(a, vb, &a.ctr->work_bwd, iter, &s_tile);
         if (t < 0) break;
@@ -317,7 +320,41 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
         for (int p = 0; p < P; ++p) {
             gC0[p] = gC1[p] = gC2[p] = gD[p] = 0.f;
             float gT = 0.f;
-            if (c.inside[p]) {
+            if (c.inside[p] && a.l1) {
+                // L1 mapping loss (Eq. 10/15/17) on this pixel: the same terms and the same
+                // FP32 operations as the separate loss kernel, so the gradients match it
+                const long long q1 = vi.pix_base + c.pix[p];
+                const long long q3 = 3 * vi.pix_base + c.pix[p];
+                const float m = a.mask ? a.mask[q1] : 1.f;
+                const float cr = m * a.kr, cd = m * a.kd, cg = m * a.kg;
+                float dpm[3] = {0.f, 0.f, 0.f};
+                if (a.t_rgb) {
+                    const float r0 = a.o_rgb[q3] - a.t_rgb[q3];
+                    const float r1 = a.o_rgb[q3 + c.HW] - a.t_rgb[q3 + c.HW];
+                    const float r2 = a.o_rgb[q3 + 2 * c.HW] - a.t_rgb[q3 + 2 * c.HW];
+                    gC0[p] = cr * l1_sign(r0);
+                    gC1[p] = cr * l1_sign(r1);
+                    gC2[p] = cr * l1_sign(r2);
+                    loss_acc += cr * fabsf(r0);
+                    loss_acc += cr * fabsf(r1);
+                    loss_acc += cr * fabsf(r2);
+                }
+                if (a.t_pointmap)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const float r = a.o_pointmap[q3 + ch * c.HW] - a.t_pointmap[q3 + ch * c.HW];
+                        dpm[ch] = cg * l1_sign(r);
+                        loss_acc += cg * fabsf(r);
+                    }
+                if (a.t_depth) {
+                    const float r = a.o_depth[q1] - a.t_depth[q1];
+                    gD[p] = cd * l1_sign(r);
+                    loss_acc += cd * fabsf(r);
+                }
+                if (a.t_pointmap)
+                    gD[p] += (px - vi.cx) / vi.fx * dpm[0] + ((float)c.j[p] - vi.cy) / vi.fy * dpm[1] + dpm[2];
+                gT = a.bg[0] * gC0[p] + a.bg[1] * gC1[p] + a.bg[2] * gC2[p];
+            } else if (c.inside[p]) {
                 const long long q1 = vi.pix_base + c.pix[p];
                 const long long q3 = 3 * vi.pix_base + c.pix[p];
                 if (a.d_rgb) {
@@ -444,6 +481,19 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
         }
     }
     if (COUNT) atomicAdd(&a.ctr->bwd_processed, n_proc);
+    if (a.l1) {
+        // this CTA's loss partial, warps summed in a fixed order
+        __shared__ float s_loss[NW];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+        if (lane == 0) s_loss[warp] = loss_acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float x = 0.f;
+            for (int w = 0; w < NW; ++w) x += s_loss[w];
+            a.loss_partial[blockIdx.x] = x;
+        }
+    }
 }
 
 size_t fwd_smem(int batch) { return (size_t)batch * (3 * sizeof(float4)); }

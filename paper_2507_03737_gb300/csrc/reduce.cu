@@ -189,10 +189,21 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const LossArgs a, co
     }
 }
 
-__global__ void __launch_bounds__(256) loss_final_kernel(const float *partial, int n, float *loss) {
-    __shared__ float s[8];
-    float acc = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+// One block: fixed-order sum of the loss partials, four independent loads in
+// flight per thread so that a long partial list is not latency-bound.
+constexpr int kFinalThreads = 1024;
+__global__ void __launch_bounds__(kFinalThreads) loss_final_kernel(const float *partial, int n, float *loss) {
+    __shared__ float s[kFinalThreads / 32];
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int i = threadIdx.x;
+    for (; i + 3 * kFinalThreads < n; i += 4 * kFinalThreads) {
+        a0 += partial[i];
+        a1 += partial[i + kFinalThreads];
+        a2 += partial[i + 2 * kFinalThreads];
+        a3 += partial[i + 3 * kFinalThreads];
+    }
+    for (; i < n; i += kFinalThreads) a0 += partial[i];
+    float acc = (a0 + a1) + (a2 + a3);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -200,7 +211,7 @@ __global__ void __launch_bounds__(256) loss_final_kernel(const float *partial, i
     __syncthreads();
     if (threadIdx.x == 0) {
         float x = 0.f;
-        for (int w = 0; w < 8; ++w) x += s[w];
+        for (int w = 0; w < kFinalThreads / 32; ++w) x += s[w];
         *loss = x;
     }
 }
@@ -228,7 +239,12 @@ cudaError_t launch_loss(const LossArgs &a, const ViewBatch &vb, cudaStream_t s) 
     else loss_kernel<1><<<grid, kLossThreads, 0, s>>>(a, vb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    loss_final_kernel<<<1, 256, 0, s>>>(a.partial, loss_blocks_per_view() * vb.n_views, a.loss);
+    loss_final_kernel<<<1, kFinalThreads, 0, s>>>(a.partial, loss_blocks_per_view() * vb.n_views, a.loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_final(const float *partial, int n, float *loss, cudaStream_t s) {
+    loss_final_kernel<<<1, kFinalThreads, 0, s>>>(partial, n, loss);
     return cudaGetLastError();
 }
 

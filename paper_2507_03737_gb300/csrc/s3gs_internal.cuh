@@ -282,6 +282,14 @@ struct BlendArgs {
     int ppt;            // pixels per thread (1, 2 or 4)
     int counting;
     int geom_only;      // backward: only the geometry slots (u, v, conic, z) are needed
+    // backward with the L1 mapping loss fused in (l1 != 0): the upstream gradients
+    // are formed per pixel from the forward's outputs and the targets instead of
+    // being read, and each CTA writes its share of the loss to loss_partial
+    int l1;
+    const float *o_rgb, *o_depth, *o_pointmap;  // the forward's outputs
+    const float *t_rgb, *t_depth, *t_pointmap, *mask;
+    float kr, kd, kg;                           // w_rgb / (3 P), w_depth / P, w_geo / (3 P)
+    float *loss_partial;                        // [gridDim.x]
 };
 cudaError_t launch_blend_fwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
 cudaError_t launch_blend_bwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
@@ -330,6 +338,8 @@ struct LossArgs {
 };
 int loss_blocks_per_view();
 cudaError_t launch_loss(const LossArgs &a, const ViewBatch &vb, cudaStream_t s);
+// Fixed-order sum of n loss partials into *loss (one block).
+cudaError_t launch_loss_final(const float *partial, int n, float *loss, cudaStream_t s);
 
 // Context access for entry points defined outside api.cu: record an error
 // message on the context and return the status; the context's device.

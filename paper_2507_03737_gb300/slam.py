@@ -152,10 +152,9 @@ class PoseRefiner:
                              p["sh_degree"])
         B.s3gs_render_fwd(R.ctx, R.state, g, self.cam_arr, self.V, self.T, self.options, self.out["rgb"], None,
                           None, None)
-        B.s3gs_mapping_loss(R.ctx, self.cam_arr, self.V, self.out["rgb"], None, None, self.target, None, None,
-                            self.weight, 1.0, 0.0, 0.0, self.d_rgb, None, None, self.loss)
-        B.s3gs_render_bwd(R.ctx, R.state, self.d_rgb, None, None, None, None, None, None, None, None,
-                          self.d_twist, 0)
+        # weighted L1 photometric loss fused into the pose-only backward
+        B.s3gs_render_bwd_l1(R.ctx, R.state, self.out["rgb"], None, None, self.target, None, None, self.weight,
+                             1.0, 0.0, 0.0, self.loss, None, None, None, None, None, self.d_twist, 0)
         B.s3gs_pose_update(R.ctx, self.V, self.d_twist, self.hp, self.m, self.v, self.step, self.T)
 
     def run_eager(self, iters=None):
@@ -247,13 +246,12 @@ class MapOptimizer:
                               p["sh_degree"])
         B.s3gs_render_fwd(R.ctx, R.state, gs, self.cam_arr, self.V, self.T, self.options, self.out["rgb"],
                           self.out["depth"], self.out["pointmap"], None)
-        B.s3gs_mapping_loss(R.ctx, self.cam_arr, self.V, self.out["rgb"], self.out["depth"], self.out["pointmap"],
-                            self.t_rgb, self.t_depth, self.t_pm, None, self.alpha,
-                            self.w_depth if self.t_depth is not None else 0.0,
-                            (1.0 - self.alpha) if self.t_pm is not None else 0.0,
-                            self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], self.loss)
-        B.s3gs_render_bwd(R.ctx, R.state, self.dout["rgb"], self.dout["depth"], self.dout["pointmap"], None,
-                          g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["colors"], self.d_twist, 0)
+        # mapping loss (Eq. 17) fused into the backward
+        B.s3gs_render_bwd_l1(R.ctx, R.state, self.out["rgb"], self.out["depth"], self.out["pointmap"], self.t_rgb,
+                             self.t_depth, self.t_pm, None, self.alpha,
+                             self.w_depth if self.t_depth is not None else 0.0,
+                             (1.0 - self.alpha) if self.t_pm is not None else 0.0, self.loss,
+                             g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["colors"], self.d_twist, 0)
         B.s3gs_map_adam_step(R.ctx, p, g, self.m, self.v, self.step, self.hp)
         B.s3gs_pose_update(R.ctx, self.V, self.d_twist, self.pose_hp, self.pm_, self.pv_, self.pstep, self.T,
                            None, self.frozen)

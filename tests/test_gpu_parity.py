@@ -415,3 +415,47 @@ def test_pose_only_backward_matches_the_full_twist(R):
         assert set(pose) == {"twist"}
         np.testing.assert_allclose(pose["twist"], full["twist"], rtol=1e-5,
                                    atol=1e-6 * float(np.abs(full["twist"]).max()))
+
+
+@pytest.mark.parametrize("det,masked,terms", [(1, False, "all"), (0, True, "all"), (1, True, "rgb_geo")])
+def test_fused_loss_backward_matches_loss_then_backward(R, det, masked, terms):
+    """s3gs_render_bwd_l1 equals s3gs_mapping_loss followed by s3gs_render_bwd: same
+    gradients (deterministic mode: up to FP32 contraction order of the pointmap term,
+    1e-6 relative per tensor; atomic mode: summation order, 1e-5), loss within 1e-5."""
+    import torch
+    from paper_2507_03737_gb300 import binding as B
+    sc = scenes.tiny_scene(7, n=300, width=77, height=45, n_views=3, scale=0.2)
+    sc.cameras[1] = dict(sc.cameras[1], width=33, height=70)
+    tgt_sc = scenes.perturb_scene(sc, 9, sigma_pos=0.05, sigma_col=0.1)
+    opt = B.s3gs_options_default(deterministic=det)
+    p_t = R.upload(tgt_sc)
+    tgt = {k: v.clone() for k, v in R.forward(p_t, sc.cameras, options=opt).items()}
+    p = R.upload(sc)
+    P = sum(c["width"] * c["height"] for c in sc.cameras)
+    mask = torch.from_numpy(np.random.default_rng(2).uniform(0, 1, P).astype(np.float32)).cuda() if masked else None
+    t_depth = tgt["depth"] if terms == "all" else None
+    cams = B.make_cameras(sc.cameras)
+
+    def grads():
+        return {k: torch.zeros_like(p[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "colors")} | \
+            {"twist": torch.zeros((3, 6), device="cuda")}
+    out = R.forward(p, sc.cameras, options=opt)
+    d = {k: torch.empty_like(out[k]) for k in ("rgb", "depth", "pointmap")}
+    loss_a = torch.zeros(1, device="cuda")
+    B.s3gs_mapping_loss(R.ctx, cams, 3, out["rgb"], out["depth"], out["pointmap"], tgt["rgb"], t_depth,
+                        tgt["pointmap"], mask, 0.98, 0.02, 0.02, d["rgb"], d["depth"], d["pointmap"], loss_a)
+    ga = grads()
+    B.s3gs_render_bwd(R.ctx, R.state, d["rgb"], d["depth"], d["pointmap"], None, ga["means"], ga["log_scales"],
+                      ga["quats"], ga["opacity_logits"], ga["colors"], ga["twist"], 0)
+    out2 = R.forward(p, sc.cameras, options=opt)
+    gb = grads()
+    loss_b = torch.zeros(1, device="cuda")
+    B.s3gs_render_bwd_l1(R.ctx, R.state, out2["rgb"], out2["depth"], out2["pointmap"], tgt["rgb"], t_depth,
+                         tgt["pointmap"], mask, 0.98, 0.02, 0.02, loss_b, gb["means"], gb["log_scales"], gb["quats"],
+                         gb["opacity_logits"], gb["colors"], gb["twist"], 0)
+    torch.cuda.synchronize()
+    tol = 1e-6 if det else 1e-5
+    for k in ga:
+        a, b = ga[k].cpu().numpy().astype(np.float64), gb[k].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(a - b) <= tol * max(np.linalg.norm(a), 1e-30), k
+    assert abs(float(loss_a[0]) - float(loss_b[0])) <= 1e-5 * abs(float(loss_a[0]))
