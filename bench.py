@@ -561,7 +561,9 @@ def run_native(args):
                "sample": f"FP64 oracle fwd+bwd on a {crop[0]}x{crop[1]} crop of view 0 ({dt:.1f} s), "
                          f"pixel-extrapolated to whole views"}
 
-    launches_per_step = 12 + (3 if args.blocks_per_sm > 0 else 0) + (1 if args.deterministic else 0)
+    # project, 3 scan kernels, emit, tile_sort, blend_fwd, blend_bwd (with the fused loss), the loss sum,
+    # project_bwd, twist_reduce; + 3 tile-order kernels (persistent grid), + det_reduce (deterministic)
+    launches_per_step = 11 + (3 if wl.opt.blocks_per_sm > 0 else 0) + (1 if args.deterministic else 0)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
