@@ -219,6 +219,162 @@ __global__ void __launch_bounds__(kAlignThreads)
     }
 }
 
+// The same pass for a compile-time patch size PP (the paper's P = 10): each
+// thread holds its column of both maps (3 PP values each) in registers, loaded
+// all at once, so only the per-column partial sums and the patch statistics go
+// through shared memory. Decisions and partials are computed by the same
+// formulas as align_pass_kernel.
+template <int PP>
+__global__ void __launch_bounds__(kAlignThreads)
+    align_pass_reg_kernel(const float *__restrict__ Xr, const float *__restrict__ Xp, const float *__restrict__ sigma,
+                          AlignPartial *__restrict__ part, unsigned char *__restrict__ cp_mask,
+                          const __grid_constant__ AlignBatch b) {
+    constexpr int ppc = kAlignThreads / PP, maxc = ppc * PP;
+    __shared__ float s_col[2][maxc];
+    __shared__ float s_mu[2][ppc], s_sd[2][ppc];
+    __shared__ int s_cand[ppc];
+    __shared__ float s_red[3][kAlignThreads / 32];
+    const int unit = blockIdx.x;
+    int v = 0;
+    while (v + 1 < b.n_views && b.v[v + 1].unit_base <= unit) ++v;
+    const AlignView &vw = b.v[v];
+    const int local = unit - vw.unit_base;
+    const int band = local / vw.chunks, chunk = local - band * vw.chunks;
+    const int y0 = band * PP, rows = min(PP, vw.h - y0);
+    const int x0 = chunk * maxc, ncols = min(maxc, vw.w - x0);
+    const int npatch = (ncols + PP - 1) / PP;
+    const long long HW = (long long)vw.w * vw.h;
+    const float s = sigma[v];
+    const int t = threadIdx.x;
+    const bool col = t < ncols;
+    const int j = t / PP;
+    float xr[3][PP], xp[3][PP];
+    if (col) {
+        const float *rc = Xr + 3 * vw.pix_base + (long long)y0 * vw.w + x0 + t;
+        const float *pc = Xp + 3 * vw.pix_base + (long long)y0 * vw.w + x0 + t;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int y = 0; y < PP; ++y) {
+                const bool in = y < rows;
+                const long long off = c * HW + (long long)y * vw.w;
+                xr[c][y] = in ? __ldg(rc + off) : 0.f;
+                xp[c][y] = in ? __ldg(pc + off) : 0.f;
+            }
+        float a = 0.f, q = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int y = 0; y < PP; ++y)
+                if (y < rows) {
+                    a += xr[c][y];
+                    q += xp[c][y];
+                }
+        s_col[0][t] = a;
+        s_col[1][t] = q;
+    }
+    __syncthreads();
+    if (t < npatch) {
+        const int c0 = t * PP, c1 = min(c0 + PP, ncols);
+        float a = 0.f, q = 0.f;
+        for (int x = c0; x < c1; ++x) {
+            a += s_col[0][x];
+            q += s_col[1][x];
+        }
+        const float nval = (float)(3 * rows * (c1 - c0));
+        s_mu[0][t] = a / nval;
+        s_mu[1][t] = s * (q / nval);
+    }
+    __syncthreads();
+    if (col) {
+        const float mr = s_mu[0][j], mp = s_mu[1][j];
+        float a = 0.f, q = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int y = 0; y < PP; ++y)
+                if (y < rows) {
+                    const float dr = xr[c][y] - mr;
+                    const float dp = fmaf(s, xp[c][y], -mp);
+                    a = fmaf(dr, dr, a);
+                    q = fmaf(dp, dp, q);
+                }
+        s_col[0][t] = a;
+        s_col[1][t] = q;
+    }
+    __syncthreads();
+    if (t < npatch) {
+        const int c0 = t * PP, c1 = min(c0 + PP, ncols);
+        float a = 0.f, q = 0.f;
+        for (int x = c0; x < c1; ++x) {
+            a += s_col[0][x];
+            q += s_col[1][x];
+        }
+        const float nval = (float)(3 * rows * (c1 - c0));
+        const float sd_r = sqrtf(a / nval), sd_p = sqrtf(q / nval);
+        const float mr = s_mu[0][t], mp = s_mu[1][t];
+        const bool cand = fabsf(mr - mp) < b.delta_mu * mp && fabsf(sd_r - sd_p) < b.delta_sigma * sd_p;
+        s_sd[0][t] = cand ? 1.0f / sd_r : 0.f;
+        s_sd[1][t] = cand ? 1.0f / sd_p : 0.f;
+        s_cand[t] = cand;
+    }
+    __syncthreads();
+    float acc_r = 0.f, acc_p = 0.f;
+    unsigned cnt = 0;
+    if (col) {
+        const bool cand = s_cand[j] != 0;
+        const float mr = s_mu[0][j], mp = s_mu[1][j], isr = s_sd[0][j], isp = s_sd[1][j];
+        unsigned char *mrow = cp_mask ? cp_mask + vw.pix_base + (long long)y0 * vw.w + x0 + t : nullptr;
+#pragma unroll
+        for (int y = 0; y < PP; ++y) {
+            if (y >= rows) break;
+            bool cp = false;
+            if (cand) {
+                float d2 = 0.f, vr = 0.f, vp = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float e = (xr[c][y] - mr) * isr - fmaf(s, xp[c][y], -mp) * isp;
+                    d2 = fmaf(e, e, d2);
+                    vr += xr[c][y];
+                    vp += xp[c][y];
+                }
+                cp = sqrtf(d2) < b.eps_r;
+                if (cp) {
+                    acc_r += vr;
+                    acc_p += vp;
+                    ++cnt;
+                }
+            }
+            if (mrow) mrow[(long long)y * vw.w] = cp ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_r += __shfl_xor_sync(0xffffffffu, acc_r, o);
+        acc_p += __shfl_xor_sync(0xffffffffu, acc_p, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((t & 31) == 0) {
+        s_red[0][t >> 5] = acc_r;
+        s_red[1][t >> 5] = acc_p;
+        s_red[2][t >> 5] = __uint_as_float(cnt);
+    }
+    __syncthreads();
+    if (t == 0) {
+        AlignPartial out;
+        out.sum_r = 0.f;
+        out.sum_p = 0.f;
+        out.count = 0;
+        out.pad = 0;
+        for (int w = 0; w < kAlignThreads / 32; ++w) {
+            out.sum_r += s_red[0][w];
+            out.sum_p += s_red[1][w];
+            out.count += __float_as_uint(s_red[2][w]);
+        }
+        part[unit] = out;
+    }
+}
+
 // One CTA per view: fixed-order double sum of the view's partials, then the
 // factor update of Algorithm 1 (an empty CP keeps the previous factor).
 __global__ void __launch_bounds__(kAlignThreads)
@@ -434,8 +590,12 @@ s3gs_status s3gs_scale_align(s3gs_ctx *ctx, const int32_t *view_wh, int32_t n_vi
     align_init_kernel<<<1, S3GS_MAX_VIEWS, 0, s>>>(sigma_init, sigma, n_views);
     for (int it = 0; it < params->max_iter; ++it) {
         const bool last = it + 1 == params->max_iter;
-        align_pass_kernel<<<b.total_units, kAlignThreads, smem, s>>>(X_r, X_p, sigma, part,
-                                                                     last ? cp_mask : nullptr, b);
+        if (b.P == 10)
+            align_pass_reg_kernel<10><<<b.total_units, kAlignThreads, 0, s>>>(X_r, X_p, sigma, part,
+                                                                             last ? cp_mask : nullptr, b);
+        else
+            align_pass_kernel<<<b.total_units, kAlignThreads, smem, s>>>(X_r, X_p, sigma, part,
+                                                                         last ? cp_mask : nullptr, b);
         align_update_kernel<<<n_views, kAlignThreads, 0, s>>>(part, sigma, last ? reinterpret_cast<long long *>(n_cp)
                                                                                 : nullptr,
                                                               last ? insufficient : nullptr, b);
