@@ -264,7 +264,6 @@ class Workload:
         torch.cuda.synchronize()
         self.tgt = {k: v.clone() for k, v in tgt.items()}
         self.out = self.R.empty_outputs(self.cams)
-        self.dout = {k: torch.zeros_like(v) for k, v in self.out.items() if k != "alpha"}
         self.grads = {k: torch.zeros_like(self.p[k]) for k in ("means", "log_scales", "quats", "opacity_logits",
                                                               "colors")}
         self.grads["twist"] = torch.zeros((self.V, 6), device=device)

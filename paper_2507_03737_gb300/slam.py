@@ -134,7 +134,6 @@ class PoseRefiner:
         self.target = target_rgb.contiguous()
         self.weight = weight.contiguous() if weight is not None else None
         self.out = renderer.empty_outputs(cameras, which=("rgb",))
-        self.d_rgb = torch.zeros_like(self.out["rgb"])
         self.d_twist = torch.zeros((self.V, 6), device=dev)
         self.loss = torch.zeros(1, device=dev)
         self.cam_arr = B.make_cameras(self.cameras)
@@ -233,7 +232,6 @@ class MapOptimizer:
         self.pv_ = torch.zeros((self.V, 6), device=dev)
         self.pstep = torch.zeros(self.V, dtype=torch.int32, device=dev)
         self.out = renderer.empty_outputs(cameras)
-        self.dout = {k: torch.zeros_like(v) for k, v in self.out.items() if k != "alpha"}
         self.grads = {k: torch.zeros_like(params[k]) for k in B.MAP_TENSORS}
         self.d_twist = torch.zeros((self.V, 6), device=dev)
         self.loss = torch.zeros(1, device=dev)
