@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--n", type=int, default=0, help="Gaussian count override (0 = the config's own; for small "
+                    "profiling cases of a config's distribution)")
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--ppt", type=int, default=0, help="pixels per forward-blend thread (0 = library default)")
@@ -207,7 +209,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2507_03737_gb300 import scenes
-    sc = scenes.config_scene(args.config)
+    sc = scenes.config_scene(args.config, n_override=args.n or None)
     crop = tile_shape(args.crop)
     crop = (max(4, crop[0] // 2), max(4, crop[1] // 2))
     times = []
@@ -361,7 +363,7 @@ def run_native(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=device)
 
-    sc = scenes.config_scene(args.config)
+    sc = scenes.config_scene(args.config, n_override=args.n or None)
     wl = Workload(sc, args, device)
     R = wl.R
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > 129 MB L2
