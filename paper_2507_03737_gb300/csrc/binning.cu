@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
 // shuffles; only the longer steps go through shared memory with block barriers.
 constexpr int kSortThreads = 256;
 constexpr int kSortCap = 4096;  // keys sorted entirely in shared memory (32 KB)
-constexpr unsigned kSegKeys = 64;  // target segment length for the warp register sorts
+constexpr unsigned kSegKeys = 24;  // window that merges buckets into segments for the warp sorts
 constexpr unsigned long long kInfKey = ~0ull;
 
 __device__ __forceinline__ unsigned ceil_log2(unsigned n) { return n <= 1 ? 0 : 32 - __clz(n - 1); }
@@ -324,43 +324,56 @@ __device__ __forceinline__ void inlane_step(unsigned long long (&x)[R]) {
     }
 }
 
-template <int R>
-__device__ __forceinline__ void regR_step(unsigned long long (&x)[R], unsigned m, bool flip) {
-    const unsigned lane = threadIdx.x & 31u;
-    if (m < (unsigned)R) {
-        switch (m) {
-        case 1: inlane_step<R, 1>(x); break;
-        case 2: if constexpr (R > 2) inlane_step<R, 2>(x); break;
-        case 3: if constexpr (R > 2) inlane_step<R, 3>(x); break;
-        case 4: if constexpr (R > 4) inlane_step<R, 4>(x); break;
-        case 5: if constexpr (R > 4) inlane_step<R, 5>(x); break;
-        case 6: if constexpr (R > 4) inlane_step<R, 6>(x); break;
-        case 7: if constexpr (R > 4) inlane_step<R, 7>(x); break;
-        default: break;
-        }
-        return;
-    }
-    unsigned long long y[R];
-    if (flip) {
-        const unsigned lm = (m + 1) / R - 1, top = ((m + 1) / R) >> 1;
-        const bool lower = (lane & top) == 0;
-#pragma unroll
-        for (int h = 0; h < R; ++h) y[h] = __shfl_xor_sync(0xffffffffu, x[h ^ (R - 1)], lm);
-#pragma unroll
-        for (int h = 0; h < R; ++h) x[h] = pick(lower, x[h], y[h]);
+// One comparator step of the network: partner = e ^ M (a flip step, which also
+// mirrors h) or e ^ M for a power of two M (a cleaner step). M is known at
+// compile time, so a whole network unrolls into straight-line shuffles and
+// selects.
+template <int R, unsigned M, bool FLIP>
+__device__ __forceinline__ void regR_step(unsigned long long (&x)[R]) {
+    if constexpr (M < (unsigned)R) {
+        inlane_step<R, (int)M>(x);
     } else {
-        const unsigned lm = m / R;
-        const bool lower = (lane & lm) == 0;
+        const unsigned lane = threadIdx.x & 31u;
+        unsigned long long y[R];
+        if constexpr (FLIP) {
+            constexpr unsigned lm = (M + 1) / R - 1, top = ((M + 1) / R) >> 1;
+            const bool lower = (lane & top) == 0;
 #pragma unroll
-        for (int h = 0; h < R; ++h) y[h] = __shfl_xor_sync(0xffffffffu, x[h], lm);
+            for (int h = 0; h < R; ++h) y[h] = __shfl_xor_sync(0xffffffffu, x[h ^ (R - 1)], lm);
 #pragma unroll
-        for (int h = 0; h < R; ++h) x[h] = pick(lower, x[h], y[h]);
+            for (int h = 0; h < R; ++h) x[h] = pick(lower, x[h], y[h]);
+        } else {
+            constexpr unsigned lm = M / R;
+            const bool lower = (lane & lm) == 0;
+#pragma unroll
+            for (int h = 0; h < R; ++h) y[h] = __shfl_xor_sync(0xffffffffu, x[h], lm);
+#pragma unroll
+            for (int h = 0; h < R; ++h) x[h] = pick(lower, x[h], y[h]);
+        }
     }
 }
 
-// Sort of one key segment of length 2 <= n <= 32 R by one warp in registers.
-template <int R>
-__device__ __forceinline__ void sort_segment_warpR(unsigned long long *g, unsigned n) {
+template <int R, int LD>
+__device__ __forceinline__ void net_cleaners(unsigned long long (&x)[R]) {
+    if constexpr (LD >= 0) {
+        regR_step<R, (1u << LD), false>(x);
+        net_cleaners<R, LD - 1>(x);
+    }
+}
+
+template <int R, int LS, int LSMAX>
+__device__ __forceinline__ void net_stages(unsigned long long (&x)[R]) {
+    if constexpr (LS <= LSMAX) {
+        regR_step<R, (1u << LS) - 1, true>(x);
+        net_cleaners<R, LS - 2>(x);
+        net_stages<R, LS + 1, LSMAX>(x);
+    }
+}
+
+// Sort of one key segment of length n <= 2^LSMAX <= 32 R by one warp with an
+// unrolled network.
+template <int R, int LSMAX>
+__device__ __forceinline__ void sort_segment_net(unsigned long long *g, unsigned n) {
     const unsigned lane = threadIdx.x & 31u;
     unsigned long long x[R];
 #pragma unroll
@@ -368,15 +381,26 @@ __device__ __forceinline__ void sort_segment_warpR(unsigned long long *g, unsign
         const unsigned e = R * lane + h;
         x[h] = e < n ? g[e] : kInfKey;
     }
-    const unsigned lsmax = ceil_log2(n);
-    for (unsigned ls = 1; ls <= lsmax; ++ls) {
-        regR_step<R>(x, (1u << ls) - 1, true);
-        for (int ld = (int)ls - 2; ld >= 0; --ld) regR_step<R>(x, 1u << ld, false);
-    }
+    net_stages<R, 1, LSMAX>(x);
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const unsigned e = R * lane + h;
         if (e < n) g[e] = x[h];
+    }
+}
+
+// Warp sort of a segment of 2 <= n <= 256 keys: the network of the smallest
+// power of two that holds it, one key per lane up to 32 keys.
+__device__ __forceinline__ void sort_segment_warp(unsigned long long *g, unsigned n) {
+    switch (ceil_log2(n)) {
+    case 1: sort_segment_net<1, 1>(g, n); break;
+    case 2: sort_segment_net<1, 2>(g, n); break;
+    case 3: sort_segment_net<1, 3>(g, n); break;
+    case 4: sort_segment_net<1, 4>(g, n); break;
+    case 5: sort_segment_net<1, 5>(g, n); break;
+    case 6: sort_segment_net<2, 6>(g, n); break;
+    case 7: sort_segment_net<4, 7>(g, n); break;
+    default: sort_segment_net<8, 8>(g, n); break;
     }
 }
 
@@ -490,48 +514,116 @@ __device__ void sort_segment_smem(unsigned long long *k, unsigned n) {
     }
 }
 
-// One CTA per tile: its depth buckets are sorted independently - buckets of up
-// to 64 keys by single warps in registers, larger ones by the whole block. A
-// tile of up to kSortCap keys is staged in shared memory with one coalesced
-// load and stored back with one coalesced store; heavier tiles sort their
-// buckets in place in global memory.
+// Refinement of a staged tile's depth buckets: a bucket of n_b > kSubKeys keys
+// is split by the next r_b = ceil(log2(ceil(n_b / kSubKeys))) bits of the depth
+// below its bin into 2^r_b sub-bins (the two clamped end bins, whose keys may
+// span several exponents, are never split). 2^r_b < 2 n_b / kSubKeys for a
+// split bucket, so a tile of at most kSortCap keys has fewer than
+// kDepthBins + 2 kSortCap / kSubKeys sub-bins. Keys of a lower sub-bin precede
+// those of a higher one, as keys of a lower bin precede those of a higher bin.
+constexpr unsigned kSubKeys = 8;
+constexpr int kMaxSub = kDepthBins + 2 * kSortCap / (int)kSubKeys;
+constexpr int kSubPerThread = kMaxSub / kSortThreads;
+static_assert(kMaxSub % kSortThreads == 0, "sub-bins are scanned kSubPerThread per thread");
+
+__device__ __forceinline__ unsigned sub_bin(unsigned zb, const unsigned short *s_sb, const unsigned char *s_r) {
+    const unsigned b = (unsigned)depth_bin(__uint_as_float(zb));
+    return s_sb[b] + ((zb & 0x7ffffu) >> (19u - s_r[b]));
+}
+
+// One CTA per tile. A tile of up to kSortCap keys is staged in shared memory:
+// its keys are counted and scattered into refined depth sub-bins, which are
+// then sorted as segments - up to 256 keys by single warps in registers, longer
+// ones by the whole block - and stored back with one coalesced store. Heavier
+// tiles sort their emission buckets in place in global memory.
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const SortArgs a) {
     __shared__ unsigned long long s_k[kSortCap];
     __shared__ unsigned s_start[kDepthBins + 1];
-    __shared__ unsigned s_seg[kDepthBins + 1];
+    __shared__ unsigned s_seg[kMaxSub + 1];        // sub-bin cursors, then segment starts
+    __shared__ unsigned short s_sub[kMaxSub + 1];  // sub-bin starts
+    __shared__ unsigned short s_sb[kDepthBins];    // first sub-bin of each bucket
+    __shared__ unsigned char s_r[kDepthBins];      // refinement bits of each bucket
     __shared__ unsigned s_warp[33];
     if (a.ctr->overflow) return;
     const long long t = blockIdx.x;
     const unsigned *bs = a.tile_start + t * kDepthBins;
     const unsigned base = bs[0], n_tile = bs[kDepthBins] - base;
     if (n_tile <= 1) return;
-    for (int i = threadIdx.x; i <= kDepthBins; i += blockDim.x) s_start[i] = bs[i] - base;
-    const bool staged = n_tile <= (unsigned)kSortCap;
-    unsigned long long *keys = staged ? s_k : a.keys + base;
-    if (staged)
-        for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x) s_k[i] = a.keys[base + i];
-    __syncthreads();
-    // Merge consecutive buckets into segments: a new segment starts at the first
-    // bucket beginning in each window of kSegKeys keys. Keys of an earlier bucket
-    // all precede those of a later one, so sorting a segment as a whole equals
-    // sorting its buckets one by one; segments hold about kSegKeys keys, which
-    // keeps the warps' register sorts full.
     static_assert(kSortThreads == kDepthBins, "one thread per bucket");
     const unsigned b = threadIdx.x;
-    const unsigned flag = (b == 0) || (s_start[b] / kSegKeys != s_start[b - 1] / kSegKeys);
-    unsigned n_seg;
-    const unsigned idx = block_excl_scan(flag, s_warp, &n_seg);
-    if (flag) s_seg[idx] = s_start[b];
-    if (b == 0) s_seg[n_seg] = n_tile;
+    s_start[b] = bs[b] - base;
+    if (b == 0) s_start[kDepthBins] = n_tile;
     __syncthreads();
+    const bool staged = n_tile <= (unsigned)kSortCap;
+    unsigned n_seg;
+    if (staged) {
+        const unsigned nb = s_start[b + 1] - s_start[b];
+        const unsigned r = (b == 0 || b == kDepthBins - 1 || nb <= kSubKeys)
+                               ? 0u : ceil_log2((nb + kSubKeys - 1) / kSubKeys);
+        unsigned n_sub;
+        s_sb[b] = (unsigned short)block_excl_scan(1u << r, s_warp, &n_sub);
+        s_r[b] = (unsigned char)r;
+        for (unsigned j = threadIdx.x; j < n_sub; j += blockDim.x) s_seg[j] = 0;
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x)
+            atomicAdd(&s_seg[sub_bin((unsigned)(a.keys[base + i] >> 32), s_sb, s_r)], 1u);
+        __syncthreads();
+        unsigned c[kSubPerThread], sum = 0, tot;
+#pragma unroll
+        for (int k = 0; k < kSubPerThread; ++k) {
+            const unsigned j = kSubPerThread * b + k;
+            c[k] = j < n_sub ? s_seg[j] : 0u;
+            sum += c[k];
+        }
+        unsigned ex = block_excl_scan(sum, s_warp, &tot);
+#pragma unroll
+        for (int k = 0; k < kSubPerThread; ++k) {
+            const unsigned j = kSubPerThread * b + k;
+            if (j < n_sub) {
+                s_sub[j] = (unsigned short)ex;
+                s_seg[j] = ex;
+            }
+            ex += c[k];
+        }
+        if (b == 0) s_sub[n_sub] = (unsigned short)n_tile;
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x) {
+            const unsigned long long key = a.keys[base + i];
+            s_k[atomicAdd(&s_seg[sub_bin((unsigned)(key >> 32), s_sb, s_r)], 1u)] = key;
+        }
+        __syncthreads();
+        // Merge consecutive sub-bins into segments: a new segment starts at the
+        // first sub-bin beginning in each window of kSegKeys keys. Keys of an
+        // earlier sub-bin all precede those of a later one, so sorting a segment
+        // as a whole equals sorting its sub-bins one by one; segments hold about
+        // kSegKeys keys, which keeps the warps' register sorts full.
+        unsigned f = 0, fl[kSubPerThread];
+#pragma unroll
+        for (int k = 0; k < kSubPerThread; ++k) {
+            const unsigned j = kSubPerThread * b + k;
+            fl[k] = j < n_sub && (j == 0 || s_sub[j] / kSegKeys != s_sub[j - 1] / kSegKeys);
+            f += fl[k];
+        }
+        unsigned idx = block_excl_scan(f, s_warp, &n_seg);
+#pragma unroll
+        for (int k = 0; k < kSubPerThread; ++k)
+            if (fl[k]) s_seg[idx++] = s_sub[kSubPerThread * b + k];
+        if (b == 0) s_seg[n_seg] = n_tile;
+    } else {
+        // the emission buckets themselves, merged into segments the same way
+        const unsigned flag = (b == 0) || (s_start[b] / kSegKeys != s_start[b - 1] / kSegKeys);
+        const unsigned idx = block_excl_scan(flag, s_warp, &n_seg);
+        if (flag) s_seg[idx] = s_start[b];
+        if (b == 0) s_seg[n_seg] = n_tile;
+    }
+    __syncthreads();
+    unsigned long long *keys = staged ? s_k : a.keys + base;
     const unsigned warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     bool any_large = false;
     for (unsigned i = warp; i < n_seg; i += nw) {
         const unsigned n = s_seg[i + 1] - s_seg[i];
         if (n < 2) continue;
-        if (n <= 64) sort_segment_warpR<2>(keys + s_seg[i], n);
-        else if (n <= 128) sort_segment_warpR<4>(keys + s_seg[i], n);
-        else if (n <= 256) sort_segment_warpR<8>(keys + s_seg[i], n);
+        if (n <= 256) sort_segment_warp(keys + s_seg[i], n);
         else any_large = true;
     }
     if (__syncthreads_or(any_large)) {
