@@ -70,7 +70,8 @@ struct s3gs_state {
     DevBuf<unsigned> vis_mask;
     DevBuf<float> grad2d;
     DevBuf<unsigned> tile_count, tile_start, cursor, order, scan_part;
-    DevBuf<unsigned long long> keys;
+    DevBuf<unsigned long long> keys;       // tile-sorted duplicate list
+    DevBuf<unsigned long long> keys_emit;  // emission order, read by the tile sort
     DevBuf<float> det_partial;
     DevBuf<float> T_final;
     DevBuf<unsigned> n_last;
@@ -158,6 +159,15 @@ s3gs_status grow(s3gs_ctx *ctx, DevBuf<T> &b, long long need, cudaStream_t s, co
     }
     b.cap = need;
     return S3GS_OK;
+}
+
+// The duplicate list lives in two buffers of one capacity: the emission writes
+// its buckets into keys_emit, the tile sort reads them and writes the sorted
+// list into keys.
+s3gs_status grow_keys(s3gs_ctx *ctx, s3gs_state *st, long long need, cudaStream_t s) {
+    s3gs_status r = grow(ctx, st->keys, need, s, "keys");
+    if (r != S3GS_OK) return r;
+    return grow(ctx, st->keys_emit, st->keys.cap, s, "keys_emit");
 }
 
 bool finite_cam(const s3gs_camera &c) {
@@ -360,7 +370,7 @@ void s3gs_state_destroy(s3gs_state *st) {
     if (st->ctx) cudaSetDevice(st->ctx->device);
     cudaDeviceSynchronize();
     void *bufs[] = {st->rec.p, st->ext.p, st->vis_mask.p, st->grad2d.p, st->tile_count.p, st->tile_start.p, st->cursor.p,
-                    st->order.p, st->scan_part.p, st->bucket, st->keys.p, st->det_partial.p, st->T_final.p,
+                    st->order.p, st->scan_part.p, st->bucket, st->keys.p, st->keys_emit.p, st->det_partial.p, st->T_final.p,
                     st->n_last.p, st->twist_part.p, st->loss_part.p, st->ctr};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -377,7 +387,7 @@ s3gs_status s3gs_reserve(s3gs_ctx *ctx, s3gs_state *st, int64_t n, int32_t n_vie
     s3gs_status r = ensure_forward_buffers(ctx, st, (long long)n * n_views, total_pixels, total_tiles, n_views, n,
                                            true, nullptr);
     if (r != S3GS_OK) return r;
-    if ((r = grow(ctx, st->keys, max_duplicates, nullptr, "keys")) != S3GS_OK) return r;
+    if ((r = grow_keys(ctx, st, max_duplicates, nullptr)) != S3GS_OK) return r;
     CK(cudaDeviceSynchronize(), "reserve");
     return S3GS_OK;
 }
@@ -427,7 +437,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     r = ensure_forward_buffers(ctx, st, n_rec, vb.total_pixels, vb.total_tiles, n_views, n, store, s);
     if (r != S3GS_OK) return r;
     if (!st->keys.p) {
-        if ((r = grow(ctx, st->keys, 1 << 16, s, "keys")) != S3GS_OK) return r;
+        if ((r = grow_keys(ctx, st, 1 << 16, s)) != S3GS_OK) return r;
     }
     const long long T = vb.total_tiles;
     const long long NBK = T * kDepthBins;  // (tile, depth bin) buckets
@@ -463,7 +473,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
         if (K > st->keys.cap) {
             long long want = K + K / 4 + 1024;
             if (want > S3GS_MAX_DUPLICATES) want = S3GS_MAX_DUPLICATES;
-            if ((r = grow(ctx, st->keys, want, s, "keys")) != S3GS_OK) return r;
+            if ((r = grow_keys(ctx, st, want, s)) != S3GS_OK) return r;
             CK(cudaMemsetAsync(&st->ctr->overflow, 0, sizeof(unsigned), s), "clear overflow");
         }
     }
@@ -472,7 +482,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     }
 
     EmitArgs ea;
-    ea.rec = st->rec.p; ea.ext = st->ext.p; ea.n = n; ea.cursor = st->cursor.p; ea.keys = st->keys.p;
+    ea.rec = st->rec.p; ea.ext = st->ext.p; ea.n = n; ea.cursor = st->cursor.p; ea.keys = st->keys_emit.p;
     ea.key_capacity = (unsigned long long)st->keys.cap; ea.ctr = st->ctr;
     {
         StageTimer tm(ctx, kStEmit, s);
@@ -480,7 +490,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     }
 
     SortArgs so;
-    so.tile_start = st->tile_start.p; so.keys = st->keys.p; so.n_tiles = T; so.ctr = st->ctr;
+    so.tile_start = st->tile_start.p; so.keys_in = st->keys_emit.p; so.keys = st->keys.p; so.n_tiles = T; so.ctr = st->ctr;
     {
         StageTimer tm(ctx, kStSort, s);
         CK(launch_tile_sort(so, s), "tile_sort");

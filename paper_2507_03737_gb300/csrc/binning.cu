@@ -389,7 +389,7 @@ __device__ __forceinline__ void sort_segment_net(unsigned long long *g, unsigned
     }
 }
 
-// Warp sort of a segment of 2 <= n <= 256 keys: the network of the smallest
+// Warp sort of a segment of 2 <= n <= 128 keys: the network of the smallest
 // power of two that holds it, one key per lane up to 32 keys.
 __device__ __forceinline__ void sort_segment_warp(unsigned long long *g, unsigned n) {
     switch (ceil_log2(n)) {
@@ -399,8 +399,7 @@ __device__ __forceinline__ void sort_segment_warp(unsigned long long *g, unsigne
     case 4: sort_segment_net<1, 4>(g, n); break;
     case 5: sort_segment_net<1, 5>(g, n); break;
     case 6: sort_segment_net<2, 6>(g, n); break;
-    case 7: sort_segment_net<4, 7>(g, n); break;
-    default: sort_segment_net<8, 8>(g, n); break;
+    default: sort_segment_net<4, 7>(g, n); break;
     }
 }
 
@@ -514,13 +513,14 @@ __device__ void sort_segment_smem(unsigned long long *k, unsigned n) {
     }
 }
 
-// Refinement of a staged tile's depth buckets: a bucket of n_b > kSubKeys keys
-// is split by the next r_b = ceil(log2(ceil(n_b / kSubKeys))) bits of the depth
-// below its bin into 2^r_b sub-bins (the two clamped end bins, whose keys may
-// span several exponents, are never split). 2^r_b < 2 n_b / kSubKeys for a
-// split bucket, so a tile of at most kSortCap keys has fewer than
-// kDepthBins + 2 kSortCap / kSubKeys sub-bins. Keys of a lower sub-bin precede
-// those of a higher one, as keys of a lower bin precede those of a higher bin.
+// Refinement of a tile's depth buckets: a bucket of n_b > q keys is split by
+// the next r_b = ceil(log2(ceil(n_b / q))) bits of the depth below its bin into
+// 2^r_b sub-bins (the two clamped end bins, whose keys may span several
+// exponents, are never split). 2^r_b < 2 n_b / q for a split bucket, so a tile
+// of n keys has fewer than kDepthBins + 2 n / q sub-bins: q = kSubKeys keeps a
+// tile of up to kSortCap keys within kMaxSub, and heavier tiles take
+// q = ceil(2 n / (kMaxSub - kDepthBins)). Keys of a lower sub-bin precede those
+// of a higher one, as keys of a lower bin precede those of a higher bin.
 constexpr unsigned kSubKeys = 8;
 constexpr int kMaxSub = kDepthBins + 2 * kSortCap / (int)kSubKeys;
 constexpr int kSubPerThread = kMaxSub / kSortThreads;
@@ -531,16 +531,17 @@ __device__ __forceinline__ unsigned sub_bin(unsigned zb, const unsigned short *s
     return s_sb[b] + ((zb & 0x7ffffu) >> (19u - s_r[b]));
 }
 
-// One CTA per tile. A tile of up to kSortCap keys is staged in shared memory:
-// its keys are counted and scattered into refined depth sub-bins, which are
-// then sorted as segments - up to 256 keys by single warps in registers, longer
-// ones by the whole block - and stored back with one coalesced store. Heavier
-// tiles sort their emission buckets in place in global memory.
-__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const SortArgs a) {
+// One CTA per tile. The tile's keys are counted into refined depth sub-bins and
+// scattered by sub-bin - into shared memory for a tile of up to kSortCap keys,
+// else straight into the tile's range of the output list - and the sub-bins,
+// merged into segments, are sorted: up to 128 keys by single warps in
+// registers, longer ones by the whole block. A staged tile is stored back with
+// one coalesced store.
+__global__ void __launch_bounds__(kSortThreads, 5) tile_sort_kernel(const SortArgs a) {
     __shared__ unsigned long long s_k[kSortCap];
     __shared__ unsigned s_start[kDepthBins + 1];
     __shared__ unsigned s_seg[kMaxSub + 1];        // sub-bin cursors, then segment starts
-    __shared__ unsigned short s_sub[kMaxSub + 1];  // sub-bin starts
+    __shared__ unsigned s_sub[kMaxSub + 1];        // sub-bin starts
     __shared__ unsigned short s_sb[kDepthBins];    // first sub-bin of each bucket
     __shared__ unsigned char s_r[kDepthBins];      // refinement bits of each bucket
     __shared__ unsigned s_warp[33];
@@ -548,88 +549,86 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const SortArgs 
     const long long t = blockIdx.x;
     const unsigned *bs = a.tile_start + t * kDepthBins;
     const unsigned base = bs[0], n_tile = bs[kDepthBins] - base;
-    if (n_tile <= 1) return;
+    const unsigned long long *in = a.keys_in + base;
+    if (n_tile <= 1) {
+        if (n_tile == 1 && threadIdx.x == 0) a.keys[base] = in[0];
+        return;
+    }
     static_assert(kSortThreads == kDepthBins, "one thread per bucket");
     const unsigned b = threadIdx.x;
     s_start[b] = bs[b] - base;
     if (b == 0) s_start[kDepthBins] = n_tile;
     __syncthreads();
     const bool staged = n_tile <= (unsigned)kSortCap;
-    unsigned n_seg;
-    if (staged) {
-        const unsigned nb = s_start[b + 1] - s_start[b];
-        const unsigned r = (b == 0 || b == kDepthBins - 1 || nb <= kSubKeys)
-                               ? 0u : ceil_log2((nb + kSubKeys - 1) / kSubKeys);
-        unsigned n_sub;
-        s_sb[b] = (unsigned short)block_excl_scan(1u << r, s_warp, &n_sub);
-        s_r[b] = (unsigned char)r;
-        for (unsigned j = threadIdx.x; j < n_sub; j += blockDim.x) s_seg[j] = 0;
-        __syncthreads();
-        for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x)
-            atomicAdd(&s_seg[sub_bin((unsigned)(a.keys[base + i] >> 32), s_sb, s_r)], 1u);
-        __syncthreads();
-        unsigned c[kSubPerThread], sum = 0, tot;
+    unsigned long long *keys = staged ? s_k : a.keys + base;
+    constexpr unsigned long long kSplit = kMaxSub - kDepthBins;
+    const unsigned q = staged ? kSubKeys
+                              : max(kSubKeys, (unsigned)((2ull * n_tile + kSplit - 1) / kSplit));
+    const unsigned nb = s_start[b + 1] - s_start[b];
+    const unsigned r = (b == 0 || b == kDepthBins - 1 || nb <= q)
+                           ? 0u : ceil_log2((unsigned)(((unsigned long long)nb + q - 1) / q));
+    unsigned n_sub;
+    s_sb[b] = (unsigned short)block_excl_scan(1u << r, s_warp, &n_sub);
+    s_r[b] = (unsigned char)r;
+    for (unsigned j = threadIdx.x; j < n_sub; j += blockDim.x) s_seg[j] = 0;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x)
+        atomicAdd(&s_seg[sub_bin((unsigned)(in[i] >> 32), s_sb, s_r)], 1u);
+    __syncthreads();
+    unsigned c[kSubPerThread], sum = 0, tot;
 #pragma unroll
-        for (int k = 0; k < kSubPerThread; ++k) {
-            const unsigned j = kSubPerThread * b + k;
-            c[k] = j < n_sub ? s_seg[j] : 0u;
-            sum += c[k];
-        }
-        unsigned ex = block_excl_scan(sum, s_warp, &tot);
+    for (int k = 0; k < kSubPerThread; ++k) {
+        const unsigned j = kSubPerThread * b + k;
+        c[k] = j < n_sub ? s_seg[j] : 0u;
+        sum += c[k];
+    }
+    unsigned ex = block_excl_scan(sum, s_warp, &tot);
 #pragma unroll
-        for (int k = 0; k < kSubPerThread; ++k) {
-            const unsigned j = kSubPerThread * b + k;
-            if (j < n_sub) {
-                s_sub[j] = (unsigned short)ex;
-                s_seg[j] = ex;
-            }
-            ex += c[k];
+    for (int k = 0; k < kSubPerThread; ++k) {
+        const unsigned j = kSubPerThread * b + k;
+        if (j < n_sub) {
+            s_sub[j] = ex;
+            s_seg[j] = ex;
         }
-        if (b == 0) s_sub[n_sub] = (unsigned short)n_tile;
-        __syncthreads();
-        for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x) {
-            const unsigned long long key = a.keys[base + i];
-            s_k[atomicAdd(&s_seg[sub_bin((unsigned)(key >> 32), s_sb, s_r)], 1u)] = key;
-        }
-        __syncthreads();
-        // Merge consecutive sub-bins into segments: a new segment starts at the
-        // first sub-bin beginning in each window of kSegKeys keys. Keys of an
-        // earlier sub-bin all precede those of a later one, so sorting a segment
-        // as a whole equals sorting its sub-bins one by one; segments hold about
-        // kSegKeys keys, which keeps the warps' register sorts full.
-        unsigned f = 0, fl[kSubPerThread];
-#pragma unroll
-        for (int k = 0; k < kSubPerThread; ++k) {
-            const unsigned j = kSubPerThread * b + k;
-            fl[k] = j < n_sub && (j == 0 || s_sub[j] / kSegKeys != s_sub[j - 1] / kSegKeys);
-            f += fl[k];
-        }
-        unsigned idx = block_excl_scan(f, s_warp, &n_seg);
-#pragma unroll
-        for (int k = 0; k < kSubPerThread; ++k)
-            if (fl[k]) s_seg[idx++] = s_sub[kSubPerThread * b + k];
-        if (b == 0) s_seg[n_seg] = n_tile;
-    } else {
-        // the emission buckets themselves, merged into segments the same way
-        const unsigned flag = (b == 0) || (s_start[b] / kSegKeys != s_start[b - 1] / kSegKeys);
-        const unsigned idx = block_excl_scan(flag, s_warp, &n_seg);
-        if (flag) s_seg[idx] = s_start[b];
-        if (b == 0) s_seg[n_seg] = n_tile;
+        ex += c[k];
+    }
+    if (b == 0) s_sub[n_sub] = n_tile;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x) {
+        const unsigned long long key = in[i];
+        keys[atomicAdd(&s_seg[sub_bin((unsigned)(key >> 32), s_sb, s_r)], 1u)] = key;
     }
     __syncthreads();
-    unsigned long long *keys = staged ? s_k : a.keys + base;
+    // Merge consecutive sub-bins into segments: a new segment starts at the
+    // first sub-bin beginning in each window of kSegKeys keys. Keys of an
+    // earlier sub-bin all precede those of a later one, so sorting a segment as
+    // a whole equals sorting its sub-bins one by one; segments hold about
+    // kSegKeys keys, which keeps the warps' register sorts full.
+    unsigned f = 0, fl[kSubPerThread], n_seg;
+#pragma unroll
+    for (int k = 0; k < kSubPerThread; ++k) {
+        const unsigned j = kSubPerThread * b + k;
+        fl[k] = j < n_sub && (j == 0 || s_sub[j] / kSegKeys != s_sub[j - 1] / kSegKeys);
+        f += fl[k];
+    }
+    unsigned idx = block_excl_scan(f, s_warp, &n_seg);
+#pragma unroll
+    for (int k = 0; k < kSubPerThread; ++k)
+        if (fl[k]) s_seg[idx++] = s_sub[kSubPerThread * b + k];
+    if (b == 0) s_seg[n_seg] = n_tile;
+    __syncthreads();
     const unsigned warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     bool any_large = false;
     for (unsigned i = warp; i < n_seg; i += nw) {
         const unsigned n = s_seg[i + 1] - s_seg[i];
         if (n < 2) continue;
-        if (n <= 256) sort_segment_warp(keys + s_seg[i], n);
+        if (n <= 128) sort_segment_warp(keys + s_seg[i], n);
         else any_large = true;
     }
     if (__syncthreads_or(any_large)) {
         for (unsigned i = 0; i < n_seg; ++i) {
             const unsigned n = s_seg[i + 1] - s_seg[i];
-            if (n <= 256) continue;
+            if (n <= 128) continue;
             if (staged) sort_segment_smem(s_k + s_seg[i], n);
             else sort_segment_block(a.keys + base + s_seg[i], n, s_k);
         }

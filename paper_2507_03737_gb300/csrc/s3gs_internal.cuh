@@ -247,7 +247,8 @@ cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s);
 
 struct SortArgs {
     const unsigned *tile_start;  // bucket starts
-    unsigned long long *keys;
+    const unsigned long long *keys_in;  // keys in emission order (bucketed by tile and depth bin)
+    unsigned long long *keys;           // the same keys sorted within each tile
     long long n_tiles;
     const DevCounters *ctr;
 };

@@ -233,6 +233,33 @@ def test_heavy_tile_sort_path(R):
     compare_forward(gpu, O.render_fwd(sc), sc.cameras, max_excluded=0.05)
 
 
+@pytest.mark.parametrize("n_same,n_rest", [(200, 300), (700, 400), (5000, 1000)])
+def test_equal_depth_stacks_sort_exactly(R, n_same, n_rest):
+    """A stack of Gaussians at one depth fills a single refined depth sub-bin, so
+    the tile sort meets one segment longer than a warp network holds (a block
+    sort in shared memory, or for more than 4096 keys the chunked global one);
+    equal depths must come out by ascending index."""
+    from paper_2507_03737_gb300 import binding as B
+    rng = np.random.default_rng(n_same)
+    n = n_same + n_rest
+    z = np.concatenate([np.full(n_same, 3.0), rng.uniform(2, 6, n_rest)])
+    means = np.stack([rng.uniform(-0.1, 0.1, n), rng.uniform(-0.1, 0.1, n), z], 1)
+    perm = rng.permutation(n)  # interleave the stack with the others in index order
+    sc = scenes.random_gaussians(rng, means[perm], 0, np.log(0.01), 0.3)
+    sc.cameras = [scenes.camera(32, 32, 40.0, 40.0, 15.5, 15.5)]
+    R.render_np(sc)
+    keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
+    rec = B.s3gs_debug_records(R.ctx, R.state, n)
+    qc = B.s3gs_debug_cover(R.ctx, R.state, n)
+    rk, rv, rr = O.bin_referee([(32, 32)], 16, 16, rec["xy"][:, 0], rec["xy"][:, 1], rec["extent"][:, 0],
+                               rec["extent"][:, 1], rec["rgb_depth"][:, 3], conic=rec["conic_opacity"][:, :3],
+                               q_cover=qc)
+    depth = rec["rgb_depth"][:, 3]
+    assert np.count_nonzero(depth == np.float32(3.0)) >= n_same // 2
+    assert np.diff(ranges).max() > (4096 if n_same > 4096 else n_same // 2)
+    assert np.array_equal(keys, rk) and np.array_equal(vals, rv) and np.array_equal(ranges, rr)
+
+
 def test_edge_cases(R):
     from paper_2507_03737_gb300 import binding as B
     cam = scenes.camera(20, 10, 20.0, 20.0, 9.5, 4.5)
