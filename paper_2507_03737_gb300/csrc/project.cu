@@ -332,6 +332,14 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
     // before any is used, so their latencies overlap; the visibility mask says
     // which rows exist without reading the per-record extents.
     const unsigned vis = ok ? a.vis_mask[gg] : 0u;
+    // Every seen view's row is requested into L2 up front, so the chunked loads
+    // below wait on L2 rather than on DRAM (the prefetch holds no registers).
+    for (int v = 0; v < vb.n_views; ++v)
+        if ((vis >> v) & 1u) {
+            const char *row = reinterpret_cast<const char *>(a.grad2d + ((long long)v * a.n + gg) * kGrad2d);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + 32));
+        }
     for (int i = threadIdx.x; i < 8 * S3GS_MAX_VIEWS * 6; i += blockDim.x) (&s_tw[0][0][0])[i] = 0.f;
     __syncthreads();
     constexpr int CH = D >= 2 ? 2 : 4;
