@@ -206,10 +206,11 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     Activated A;
     bool ok = activate(ls, q, a.opacity_logits[g], A) && live;
-    float k[NC * 3];
+    // Degree 0 keeps its colour in registers; higher degrees re-read their SH
+    // coefficients (L1-resident) in each view that sees the Gaussian rather
+    // than hold 3 (D + 1)^2 registers across the view loop.
     const float *cp = a.colors + (long long)g * NC * 3;
-#pragma unroll
-    for (int i = 0; i < NC * 3; ++i) k[i] = cp[i];
+    float k0[3] = {cp[0], cp[1], cp[2]};
 
     unsigned mask = 0;
     for (int v = 0; v < vb.n_views; ++v) {
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                     // colour (Eq. 2; SH for degree >= 1)
                     float col[3];
                     if (D == 0) {
-                        col[0] = k[0]; col[1] = k[1]; col[2] = k[2];
+                        col[0] = k0[0]; col[1] = k0[1]; col[2] = k0[2];
                     } else {
                         float C[3];
                         cam_centre(T, C);
@@ -269,13 +270,14 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                         float in = rsqrtf(dx * dx + dy * dy + dz * dz);
                         float Y[16];
                         sh_basis<D>(dx * in, dy * in, dz * in, Y);
+                        float c3[3] = {k0[0], k0[1], k0[2]};
 #pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            float c = k[ch];
+                        for (int i = 1; i < NC; ++i) {
 #pragma unroll
-                            for (int i = 1; i < NC; ++i) c += Y[i] * k[3 * i + ch];
-                            col[ch] = fmaxf(c, 0.0f);
+                            for (int ch = 0; ch < 3; ++ch) c3[ch] += Y[i] * __ldg(cp + 3 * i + ch);
                         }
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(c3[ch], 0.0f);
                     }
                     Record R;
                     const float lo2 = log2f(A.opacity);
