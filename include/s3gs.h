@@ -139,7 +139,8 @@ void s3gs_state_destroy(s3gs_state *state);
  * CUDA-graph capture requires): n Gaussians, n_views views, total_pixels over
  * all views, total_tiles over all views at the smallest tile used (each tile
  * holds 256 depth buckets internally), and max_duplicates (Gaussian, tile)
- * pairs. Synchronous. */
+ * pairs (16 bytes of device memory each: the emission buffer and the sorted
+ * list). Synchronous. */
 s3gs_status s3gs_reserve(s3gs_ctx *ctx, s3gs_state *state, int64_t n, int32_t n_views,
                          int64_t total_pixels, int64_t total_tiles, int64_t max_duplicates);
 
