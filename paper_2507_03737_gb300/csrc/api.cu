@@ -369,9 +369,10 @@ void s3gs_state_destroy(s3gs_state *st) {
     if (!st) return;
     if (st->ctx) cudaSetDevice(st->ctx->device);
     cudaDeviceSynchronize();
-    void *bufs[] = {st->rec.p, st->ext.p, st->vis_mask.p, st->grad2d.p, st->tile_count.p, st->tile_start.p, st->cursor.p,
-                    st->order.p, st->scan_part.p, st->bucket, st->keys.p, st->keys_emit.p, st->det_partial.p, st->T_final.p,
-                    st->n_last.p, st->twist_part.p, st->loss_part.p, st->ctr};
+    void *bufs[] = {st->rec.p,       st->ext.p,       st->vis_mask.p,  st->grad2d.p,      st->tile_count.p,
+                    st->tile_start.p, st->cursor.p,    st->order.p,     st->scan_part.p,   st->bucket,
+                    st->keys.p,      st->keys_emit.p, st->det_partial.p, st->T_final.p,   st->n_last.p,
+                    st->twist_part.p, st->loss_part.p, st->ctr};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (st->ctr_host) cudaFreeHost(st->ctr_host);
