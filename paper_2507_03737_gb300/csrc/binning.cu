@@ -572,8 +572,18 @@ __global__ void __launch_bounds__(kSortThreads, 5) tile_sort_kernel(const SortAr
     s_r[b] = (unsigned char)r;
     for (unsigned j = threadIdx.x; j < n_sub; j += blockDim.x) s_seg[j] = 0;
     __syncthreads();
-    for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x)
-        atomicAdd(&s_seg[sub_bin((unsigned)(in[i] >> 32), s_sb, s_r)], 1u);
+    // both passes over the tile's keys keep four loads in flight per thread
+    for (unsigned i0 = threadIdx.x; i0 < n_tile; i0 += 4 * blockDim.x) {
+        unsigned zb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned i = i0 + u * blockDim.x;
+            zb[u] = i < n_tile ? (unsigned)(in[i] >> 32) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u * blockDim.x < n_tile) atomicAdd(&s_seg[sub_bin(zb[u], s_sb, s_r)], 1u);
+    }
     __syncthreads();
     unsigned c[kSubPerThread], sum = 0, tot;
 #pragma unroll
@@ -594,9 +604,17 @@ __global__ void __launch_bounds__(kSortThreads, 5) tile_sort_kernel(const SortAr
     }
     if (b == 0) s_sub[n_sub] = n_tile;
     __syncthreads();
-    for (unsigned i = threadIdx.x; i < n_tile; i += blockDim.x) {
-        const unsigned long long key = in[i];
-        keys[atomicAdd(&s_seg[sub_bin((unsigned)(key >> 32), s_sb, s_r)], 1u)] = key;
+    for (unsigned i0 = threadIdx.x; i0 < n_tile; i0 += 4 * blockDim.x) {
+        unsigned long long key[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned i = i0 + u * blockDim.x;
+            key[u] = i < n_tile ? in[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u * blockDim.x < n_tile)
+                keys[atomicAdd(&s_seg[sub_bin((unsigned)(key[u] >> 32), s_sb, s_r)], 1u)] = key[u];
     }
     __syncthreads();
     // Merge consecutive sub-bins into segments: a new segment starts at the
