@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
             stage(a, rbase, b, cnt, s_p0, s_p1, s_col, nullptr);
             __syncthreads();
             for (unsigned k = 0; k < cnt && !all_done; ++k) {
-                const float4 p0 = s_p0[k], p1 = s_p1[k];
+                const float4 p0 = s_p0[k], p1 = s_p1[k], col = s_col[k];
+                const unsigned idx = b - s + k + 1;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     if (done[p]) continue;
@@ -190,13 +191,12 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
                         continue;
                     }
                     const float w = al * T[p];
-                    const float4 col = s_col[k];
                     C0[p] = fmaf(col.x, w, C0[p]);
                     C1[p] = fmaf(col.y, w, C1[p]);
                     C2[p] = fmaf(col.z, w, C2[p]);
                     D[p] = fmaf(p1.w, w, D[p]);
                     T[p] = Tn;
-                    last[p] = b - s + k + 1;
+                    last[p] = idx;
                     if (COUNT) ++n_blend;
                 }
                 all_done = true;
