@@ -127,17 +127,18 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
     __shared__ unsigned s_view[8][32];
     if (a.ctr->overflow) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)vb.n_views * a.n;
+    // blockIdx.y is the view, so no record index needs dividing
+    const int v = (int)blockIdx.y;
+    const long long gl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long r = (long long)v * a.n + gl;
     unsigned cnt = 0, origin = 0, ntx = 1, tiles_x = 0, t0 = 0, view = 0;
     unsigned long long key = 0;
     CoverEllipse ell;
     ell.u = ell.v = ell.A = ell.B = ell.C = ell.iA = ell.iC = ell.qc = 0.f;
-    if (r < total) {
+    if (gl < a.n) {
         const int2 ext = a.ext[r];
         if (ext.x > 0) {
-            const int v = (int)(r / a.n);
-            const unsigned g = (unsigned)(r - (long long)v * a.n);
+            const unsigned g = (unsigned)gl;
             const ViewInfo &vi = vb.v[v];
             const float4 ra = a.rec[r].a;
             const float4 rb = a.rec[r].b;
@@ -190,7 +191,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
                     if (s_incl[warp][src + b - 1] <= j) src += b;
                 const unsigned local = j - s_excl[warp][src];
                 const unsigned nx = s_ntx[warp][src];
-                const unsigned row = local / nx, colm = local % nx;
+                unsigned colm;
+                const unsigned row = div_small(local, nx, colm);
                 const unsigned tt = s_t0[warp][src];
                 const int tx = (int)(tt & 0xffffu) + (int)colm, ty = (int)(tt >> 16) + (int)row;
                 const ViewInfo &vi = vb.v[s_view[warp][src]];
@@ -705,9 +707,8 @@ cudaError_t launch_scan(const ScanArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s) {
-    long long total = (long long)vb.n_views * a.n;
-    if (total == 0) return cudaSuccess;
-    emit_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a, vb);
+    if (vb.n_views == 0 || a.n == 0) return cudaSuccess;
+    emit_kernel<<<dim3((unsigned)((a.n + 255) / 256), (unsigned)vb.n_views), 256, 0, s>>>(a, vb);
     return cudaGetLastError();
 }
 

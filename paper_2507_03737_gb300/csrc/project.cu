@@ -183,8 +183,9 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
         const int s_ntx = __shfl_sync(0xffffffffu, ntx, src);
         const int s_bin = __shfl_sync(0xffffffffu, bin, src);
         if (j < total) {
-            const int local = (int)(j - s_excl);
-            const int tx = (int)(s_t0 & 0xffffu) + local % s_ntx, ty = (int)(s_t0 >> 16) + local / s_ntx;
+            unsigned col;
+            const unsigned row = div_small(j - s_excl, (unsigned)s_ntx, col);
+            const int tx = (int)(s_t0 & 0xffffu) + (int)col, ty = (int)(s_t0 >> 16) + (int)row;
             const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
             const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
             if (tile_hit(e, px0, px1, py0, py1))

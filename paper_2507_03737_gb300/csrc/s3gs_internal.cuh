@@ -37,6 +37,19 @@ constexpr int kGrad2d = 10;          // per-record 2D gradient slots
 // each sorted, concatenate to the tile's list in (depth, index) order; bucket b
 // of tile t has id t * 256 + b.
 constexpr int kDepthBins = 256;
+
+// q = floor(x / d) and r = x - q d for x < 2^24, d >= 1, without an integer
+// division: both roundings toward zero make the float estimate a lower bound,
+// off by less than 4 / d, and the loop adds what it is short of.
+__device__ __forceinline__ unsigned div_small(unsigned x, unsigned d, unsigned &r) {
+    unsigned q = __float2uint_rz(__fmul_rz(__uint2float_rz(x), __frcp_rz(__uint2float_rz(d))));
+    r = x - q * d;
+    while (r >= d) {
+        ++q;
+        r -= d;
+    }
+    return q;
+}
 __device__ __forceinline__ int depth_bin(float z) {
     const int b = (int)(__float_as_uint(z) >> 19) - 1993;
     return b < 0 ? 0 : (b > kDepthBins - 1 ? kDepthBins - 1 : b);
