@@ -96,12 +96,20 @@ def _twist_by_view(twist_crops, crops, n_views):
     return out
 
 
-def test_config3_full_size_window(R):
+# the library default, and the schedule the autotuner picks for config 3 (a persistent
+# heaviest-first grid of 8 CTAs per SM, 2 pixels per backward thread)
+CONFIG3_SCHEDULES = [None, dict(blocks_per_sm=8, pixels_per_thread=2, bwd_pixels_per_thread=2)]
+
+
+@pytest.mark.parametrize("schedule", CONFIG3_SCHEDULES, ids=["default", "autotuned"])
+def test_config3_full_size_window(R, schedule):
     """1M Gaussians, 12 x 1241x376, batched: forward windows and sparse-gradient backward."""
+    from paper_2507_03737_gb300 import binding as B
     sc = scenes.config_scene(3)
     w, h = 12, 8
     crops = _crops(sc.cameras, 1, w, h, seed=31)
-    ref, res = _forward_check(R, sc, crops, w, h)
+    options = None if schedule is None else B.s3gs_options_default(**schedule)
+    ref, res = _forward_check(R, sc, crops, w, h, options=options)
     assert res["pixels"] == 12 * w * h
     full_ups, crop_ups = _sparse_upstream(sc, crops, w, h, ref, seed=32)
     g = R.backward_np(full_ups, len(sc.cameras))
