@@ -36,8 +36,12 @@ FP32_LANES_PER_SM = 128
 # Blend schedules the autotuner found for a workload (autotune.py, coordinate
 # descent on CUDA-event timings), applied by default so that every run times, and
 # the committed ncu summaries profile, the same kernels: config 3 runs a persistent
-# heaviest-first grid of 8 CTAs per SM with 2 pixels per blend thread.
-TUNED_SCHEDULES = {3: {"blocks_per_sm": 8, "pixels_per_thread": 2, "bwd_pixels_per_thread": 2}}
+# heaviest-first grid of 8 CTAs per SM with 2 pixels per blend thread; the small
+# single view of config 1 fills the GPU only with 8x8 tiles of one pixel per thread.
+TUNED_SCHEDULES = {
+    1: {"tile_w": 8, "tile_h": 8, "pixels_per_thread": 1, "bwd_pixels_per_thread": 1, "batch": 64},
+    3: {"blocks_per_sm": 8, "pixels_per_thread": 2, "bwd_pixels_per_thread": 2},
+}
 
 
 def parse():
@@ -77,7 +81,8 @@ def parse():
                          "applied instead of autotuning, to time or profile one schedule")
     ap.add_argument("--autotune", type=int, default=-1,
                     help="window row: 1 = autotune the blend schedule for the workload before timing (default: "
-                         "on for configs 2 and 4; config 3 takes the schedule the autotuner found for it); "
+                         "on for configs 2 and 4; configs 1 and 3 take the schedules the autotuner found for "
+                         "them); "
                          "0 = the library's default schedule")
     return ap.parse_args()
 

@@ -72,20 +72,27 @@ def test_binning_bit_exact(R, tile):
     assert np.array_equal(ranges, rr)
 
 
-def test_forward_config1(R):
+# the library default, and the schedule bench.py times config 1 with (8x8 tiles,
+# one pixel per thread, batches of 64)
+CONFIG1_SCHEDULES = [None, dict(tile_w=8, tile_h=8, pixels_per_thread=1, bwd_pixels_per_thread=1, batch=64)]
+
+
+@pytest.mark.parametrize("schedule", CONFIG1_SCHEDULES, ids=["default", "tuned"])
+def test_forward_config1(R, schedule):
     sc = scenes.config_scene(1)
-    gpu = R.render_np(sc)
+    gpu = R.render_np(sc, options=None if schedule is None else _opts(**schedule))
     ref = O.render_fwd(sc)
     res = compare_forward(gpu, ref, sc.cameras)
     assert res["excluded"] < 100
 
 
-def test_backward_config1(R):
+@pytest.mark.parametrize("schedule", CONFIG1_SCHEDULES, ids=["default", "tuned"])
+def test_backward_config1(R, schedule):
     sc = scenes.config_scene(1)
     ref_f = O.render_fwd(sc)
     mask = pixel_mask(ref_f)
     ups = upstream(sc.cameras, 7, mask)
-    R.render_np(sc)
+    R.render_np(sc, options=None if schedule is None else _opts(**schedule))
     g = R.backward_np(ups, 1)
     gref = O.render_bwd(sc, **ups)
     compare_grads(g, gref)
