@@ -47,7 +47,7 @@ TUNED_SCHEDULES = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", type=int, default=3)
@@ -103,10 +103,18 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (at most 3 s) for the first sample, so that sampling is live when the
+        # timed region starts
+        t_end = time.monotonic() + 3.0
+        while time.monotonic() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -425,18 +433,31 @@ def run_native(args):
             wl.step_batched()
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
+        # the step itself, with no per-stage event nodes: its replays give `value`
         graph = torch.cuda.CUDAGraph()
-        B.s3gs_set_timing(R.ctx, 1)
+        B.s3gs_set_timing(R.ctx, 0)
         with torch.cuda.graph(graph):
             wl.step_batched()
         torch.cuda.synchronize()
-        torch.zeros(1, device=device)  # surfaces any error left by the capture here
+        # the same step with a start/stop event pair around every stage: replayed
+        # in alternation with the plain graph inside the timed region, it gives the
+        # per-stage times without adding its event nodes to the timed step
+        graph_staged = torch.cuda.CUDAGraph()
+        B.s3gs_set_timing(R.ctx, 1)
+        with torch.cuda.graph(graph_staged):
+            wl.step_batched()
+        torch.cuda.synchronize()
+        torch.zeros(1, device=device)  # surfaces any error left by the captures here
         batched = graph.replay
+        staged = graph_staged.replay
     else:
         B.s3gs_set_timing(R.ctx, 1)
         batched = wl.step_batched
+        staged = None
     for _ in range(args.warmup):
         batched()
+        if staged is not None:
+            staged()
     torch.cuda.synchronize()
 
     # ---- timed region: K batched steps
@@ -457,6 +478,10 @@ def run_native(args):
         e1.record()
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        if staged is not None:
+            flush()
+            staged()
+            torch.cuda.synchronize()
         try:
             for k, v in B.s3gs_read_timing(R.ctx).items():
                 stage_tot[k] = stage_tot.get(k, 0.0) + v
@@ -467,7 +492,8 @@ def run_native(args):
         dist.barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    stage_src = "graph replays of the timed region"
+    stage_src = ("replays of the same step captured with per-stage events, each after an L2 flush, alternating "
+                 "with the timed replays" if staged is not None else "the timed eager steps")
     if not stage_tot:
         # events recorded inside the graph were not readable: time the same
         # kernels in eager steps right after the timed region instead
@@ -602,7 +628,8 @@ def run_native(args):
                           "pairs_per_s_fwd_bwd": (fwd_proc + bwd_proc) * world / (ms_per_step / 1e3),
                           "blended_pairs_per_s": fwd_blend * world / (ms_per_step / 1e3)},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk, "wall_s_timed_region": wall,
+                "gpu_launches": launches_per_step * args.steps * (2 if staged is not None else 1), "clocks": clk,
+                "wall_s_timed_region": wall,
                 "paper_context": "paper reports only whole-SLAM runtimes (~5 min KITTI-07 on an RTX A6000)"}
         print(json.dumps(line), flush=True)
     R.close()
