@@ -570,10 +570,11 @@ def run_native(args):
     #   every evaluated pair: offset, quadratic form, exponent, alpha       13
     #   forward, each blended pair: transmittance, weight, 4 accumulations  10
     #   backward, each contributing pair: T restore, weight, dalpha, behind
-    #   value, 10 gradient terms and their 10 accumulations                51
-    #   (a pose-only backward skips the colour and opacity terms: 37 instead of 51)
+    #   value, 4 colour/depth accumulations and the 6 moments of
+    #   dL/dalpha * alpha (sum, dx, dy, dx^2, dx dy, dy^2)                  35
+    #   (a pose-only backward skips the colour and opacity terms: 28 instead of 35)
     flops = {"blend_fwd": 13 * fwd_proc + 10 * fwd_blend,
-             "blend_bwd": 13 * bwd_proc + (37 if wl.pose_only else 51) * fwd_blend}
+             "blend_bwd": 13 * bwd_proc + (28 if wl.pose_only else 35) * fwd_blend}
     n_rec = sc.n * wl.V
     nc = (sc.sh_degree + 1) ** 2
     p_in = 4 * (3 + 3 + 4 + 1 + 3 * nc)
@@ -878,14 +879,14 @@ def run_pose(args):
     elif dominant in ("blend_fwd", "blend_bwd"):
         # pair counts of one iteration (counting mode, outside the timed region); the
         # pose-only backward accumulates the geometry slots only: 13 flops per
-        # evaluated pair + 37 per contributing pair (the 51 of the full backward
+        # evaluated pair + 28 per contributing pair (the 35 of the full backward
         # minus the colour and opacity terms)
         B.s3gs_set_counting(R.ctx, 1)
         pr.iteration()
         cnt = B.s3gs_read_counters(R.ctx, R.state)
         B.s3gs_set_counting(R.ctx, 0)
         flops = {"blend_fwd": 13 * cnt["fwd_processed"] + 10 * cnt["fwd_blended"],
-                 "blend_bwd": 13 * cnt["bwd_processed"] + 37 * cnt["fwd_blended"]}
+                 "blend_bwd": 13 * cnt["bwd_processed"] + 28 * cnt["fwd_blended"]}
         sm_count = torch.cuda.get_device_properties(R.device).multi_processor_count
         clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = sm_count * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12

@@ -434,19 +434,22 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                     }
                     vals[kGZ] = __fmaf_rn(w, gD[p], vals[kGZ]);
                     if (!pe.clamped) {
-                        // alpha = 2^(p + log2 o): d alpha / d logit = alpha (1 - o),
-                        // d alpha / dp = alpha ln 2, with p quadratic in (dx, dy) and dx = i - u
+                        // alpha = o exp(-q/2), q = A dx^2 + 2 B dx dy + C dy^2, dx = i - u: with
+                        // g = dL/dalpha * alpha, the pair adds g (A dx + B dy) to dL/du,
+                        // g (B dx + C dy) to dL/dv, -g dx^2 / 2, -g dx dy, -g dy^2 / 2 to dL/d(A, B, C)
+                        // and g (1 - o) to dL/dlogit. The conic and o are fixed per Gaussian, so
+                        // only the moments of g are summed here (slot order of the record's
+                        // gradient row: X, Y, XX, XY, YY, S with X = sum g dx, XY = sum g dx dy,
+                        // S = sum g); the projection backward applies the per-Gaussian factors.
                         const float g = __fmul_rn(da, al);
-                        const float ngl = __fmul_rn(-kLn2, g);
-                        const float hg = __fmul_rn(-0.5f, g);
-                        if (!GEOM) vals[kGO] = __fmaf_rn(g, __fsub_rn(1.f, q1.z), vals[kGO]);
-                        vals[kGA] = __fmaf_rn(__fmul_rn(hg, pe.dx), pe.dx, vals[kGA]);
-                        vals[kGB] = __fmaf_rn(__fmul_rn(-g, pe.dx), pe.dy, vals[kGB]);
-                        vals[kGC] = __fmaf_rn(__fmul_rn(hg, pe.dy), pe.dy, vals[kGC]);
-                        const float tu = __fmaf_rn(__fmul_rn(2.f, p0.z), pe.dx, __fmul_rn(p0.w, pe.dy));
-                        const float tv = __fmaf_rn(p0.w, pe.dx, __fmul_rn(__fmul_rn(2.f, q1.x), pe.dy));
-                        vals[kGU] = __fmaf_rn(ngl, tu, vals[kGU]);
-                        vals[kGV] = __fmaf_rn(ngl, tv, vals[kGV]);
+                        const float gx = __fmul_rn(g, pe.dx);
+                        const float gy = __fmul_rn(g, pe.dy);
+                        if (!GEOM) vals[kGO] = __fadd_rn(vals[kGO], g);
+                        vals[kGA] = __fmaf_rn(gx, pe.dx, vals[kGA]);
+                        vals[kGB] = __fmaf_rn(gx, pe.dy, vals[kGB]);
+                        vals[kGC] = __fmaf_rn(gy, pe.dy, vals[kGC]);
+                        vals[kGU] = __fadd_rn(vals[kGU], gx);
+                        vals[kGV] = __fadd_rn(vals[kGV], gy);
                     }
                 }
                 if (DET) {

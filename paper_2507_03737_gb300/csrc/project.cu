@@ -393,10 +393,16 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
                 float cc = j11 * (j11 * Sc[4] + j12 * Sc[5]) + j12 * (j11 * Sc[7] + j12 * Sc[8]) + kDilation;
                 float idet = 1.0f / (ca * cc - cb * cb);
                 float cA = cc * idet, cB = -cb * idet, cC = ca * idet;
+                // the blend's moments of g = dL/dalpha * alpha -> gradients of the centre
+                // (u, v) and of the conic [[A, B], [B, C]] (alpha = o exp(-(A dx^2 + 2 B dx dy
+                // + C dy^2) / 2), dx = i - u)
+                const float gU = cA * gr[kGU] + cB * gr[kGV];
+                const float gV = cB * gr[kGU] + cC * gr[kGV];
+                const float gA = -0.5f * gr[kGA], gC = -0.5f * gr[kGC];
                 // conic -> 2D covariance: G2 = -Sinv Ginv Sinv, Ginv = [[gA, gB/2], [gB/2, gC]]
-                float hB = 0.5f * gr[kGB];
-                float t00 = cA * gr[kGA] + cB * hB, t01 = cA * hB + cB * gr[kGC];
-                float t10 = cB * gr[kGA] + cC * hB, t11 = cB * hB + cC * gr[kGC];
+                float hB = -0.5f * gr[kGB];
+                float t00 = cA * gA + cB * hB, t01 = cA * hB + cB * gC;
+                float t10 = cB * gA + cC * hB, t11 = cB * hB + cC * gC;
                 float g00 = -(t00 * cA + t01 * cB);
                 float g01 = -(t00 * cB + t01 * cC);
                 float g11 = -(t10 * cB + t11 * cC);
@@ -431,9 +437,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
                     dSig[3] += WG[4]; dSig[4] += WG[5]; dSig[5] += WG[8];
                 }
                 // camera-frame mean
-                float dp0 = gr[kGU] * fx * iz - dJ02 * fx * iz2;
-                float dp1 = gr[kGV] * fy * iz - dJ12 * fy * iz2;
-                float dp2 = -gr[kGU] * fx * px * iz2 - gr[kGV] * fy * py * iz2 + gr[kGZ] - dJ00 * fx * iz2 +
+                float dp0 = gU * fx * iz - dJ02 * fx * iz2;
+                float dp1 = gV * fy * iz - dJ12 * fy * iz2;
+                float dp2 = -gU * fx * px * iz2 - gV * fy * py * iz2 + gr[kGZ] - dJ00 * fx * iz2 +
                             2.f * dJ02 * fx * px * iz2 * iz - dJ11 * fy * iz2 + 2.f * dJ12 * fy * py * iz2 * iz;
                 dmu[0] += T[0] * dp0 + T[4] * dp1 + T[8] * dp2;
                 dmu[1] += T[1] * dp0 + T[5] * dp1 + T[9] * dp2;
@@ -532,7 +538,8 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
         float dqq[4] = {(dq[0] - w * dot) * A.qinv, (dq[1] - x * dot) * A.qinv, (dq[2] - y * dot) * A.qinv,
                         (dq[3] - z * dot) * A.qinv};
         float dls[3] = {ds[0] * A.s[0], ds[1] * A.s[1], ds[2] * A.s[2]};
-        float dol = dO;  // the blend backward accumulates dL/d(opacity logit) directly
+        // alpha = o 2^p: d alpha / d logit = alpha (1 - o), applied once to the sum of g
+        float dol = (1.0f - A.opacity) * dO;
         const bool acc = a.accumulate != 0;
         if (a.d_means) {
             float *o = a.d_means + 3 * g;

@@ -55,7 +55,12 @@ __device__ __forceinline__ int depth_bin(float z) {
     return b < 0 ? 0 : (b > kDepthBins - 1 ? kDepthBins - 1 : b);
 }
 
-// 2D gradient slot order of a record (slot kGO holds dL/d(opacity logit)).
+// 2D gradient row of a record, as the backward blend accumulates it over the
+// pixels, with g = dL/dalpha * alpha per (pixel, Gaussian) pair and (dx, dy) the
+// pixel's offset from the centre: kGU = sum g dx, kGV = sum g dy, kGA = sum g dx^2,
+// kGB = sum g dx dy, kGC = sum g dy^2, kGO = sum g (moments, turned into the
+// gradients of the centre, conic and opacity logit by the projection backward),
+// then dL/d(r, g, b) and dL/dz directly.
 enum { kGU = 0, kGV, kGA, kGB, kGC, kGO, kGR, kGG, kGBl, kGZ };
 
 struct ViewInfo {
