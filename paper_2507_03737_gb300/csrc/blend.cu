@@ -14,8 +14,12 @@
 namespace s3gs {
 namespace {
 
-// Pixel p of this thread: column t % TW, row (t / TW) P + p of tile t, so a warp
-// covers a contiguous band of rows.
+// Pixel p of a thread: one column, P adjacent rows. Where the tile allows it (TW a
+// multiple of 8 and TH / P a multiple of 4) each warp covers a compact block of
+// 8 columns x 4P rows (lane & 7 the column, lane >> 3 the row group), so that fewer
+// warps meet each Gaussian than with bands of full tile rows: fewer warps evaluate
+// pairs outside the ellipse and fewer reduce a Gaussian's gradient in the backward.
+// Otherwise thread t takes column t % TW and rows (t / TW) P + p.
 template <int TW, int TH, int P>
 struct TileCoord {
     int v;
@@ -33,10 +37,21 @@ __device__ __forceinline__ TileCoord<TW, TH, P> tile_coord(const ViewBatch &vb, 
     const ViewInfo &vi = vb.v[c.v];
     const int tl = t - vi.tile_base;
     const int ty = tl / vi.tiles_x, tx = tl - ty * vi.tiles_x;
-    c.i = tx * TW + (int)(threadIdx.x % TW);
+    constexpr bool kBlocks = TW % 8 == 0 && (TH / P) % 4 == 0;
+    int col, trow;
+    if (kBlocks) {
+        constexpr int WX = TW / 8;  // warps across the tile
+        const int lane = (int)(threadIdx.x & 31u), w = (int)(threadIdx.x >> 5);
+        col = (w % WX) * 8 + (lane & 7);
+        trow = (w / WX) * 4 + (lane >> 3);
+    } else {
+        col = (int)(threadIdx.x % TW);
+        trow = (int)(threadIdx.x / TW);
+    }
+    c.i = tx * TW + col;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        c.j[p] = ty * TH + (int)(threadIdx.x / TW) * P + p;
+        c.j[p] = ty * TH + trow * P + p;
         c.inside[p] = c.i < vi.w && c.j[p] < vi.h;
         c.pix[p] = (long long)c.j[p] * vi.w + c.i;
     }
@@ -111,7 +126,7 @@ __device__ __forceinline__ int warp_reduce_scatter10(const float v[kGrad2d], flo
     return slot + (b4 ? 5 : 0);
 }
 
-// The same for the six geometry slots (u, v, A, B, C, z) of a geometry-only
+// The same for the six geometry slots (the moments X, Y, XX, XY, YY and z) of a geometry-only
 // backward: 3 + 2 + 1 shuffles halve the lanes' values, two more finish the sums;
 // lanes with lane & 3 == 0 own one slot each (compact index 0..5, or -1).
 __device__ __forceinline__ int warp_reduce_scatter6(const float v[6], float *sum) {
