@@ -36,11 +36,12 @@ FP32_LANES_PER_SM = 128
 # Blend schedules the autotuner found for a workload (autotune.py, coordinate
 # descent on CUDA-event timings), applied by default so that every run times, and
 # the committed ncu summaries profile, the same kernels: config 3 runs a persistent
-# heaviest-first grid of 8 CTAs per SM with 2 pixels per blend thread; the small
-# single view of config 1 fills the GPU only with 8x8 tiles of one pixel per thread.
+# heaviest-first grid of 16 CTAs per SM, 2 pixels per forward and 4 per backward
+# blend thread, batches of 64 staged Gaussians; the small single view of config 1
+# fills the GPU only with 8x8 tiles of one pixel per thread.
 TUNED_SCHEDULES = {
     1: {"tile_w": 8, "tile_h": 8, "pixels_per_thread": 1, "bwd_pixels_per_thread": 1, "batch": 64},
-    3: {"blocks_per_sm": 8, "pixels_per_thread": 2, "bwd_pixels_per_thread": 2},
+    3: {"blocks_per_sm": 16, "pixels_per_thread": 2, "bwd_pixels_per_thread": 4, "batch": 64},
 }
 
 
@@ -1084,7 +1085,9 @@ def run_mapping(args):
     torch.cuda.set_device(local)
     sc = scenes.config_scene(3)
     V = len(sc.cameras)
-    R = Renderer(local)
+    # the blend schedule the window step of the same workload runs
+    sched = json.loads(args.schedule) if args.schedule else TUNED_SCHEDULES[3]
+    R = Renderer(local, B.s3gs_options_default(**sched))
     tgt = R.forward(R.upload(scenes.perturb_scene(sc, 77)), sc.cameras)
     t_rgb, t_pm = tgt["rgb"].clone(), tgt["pointmap"].clone()
     p = R.upload(sc)
@@ -1126,7 +1129,7 @@ def run_mapping(args):
             "data": "synthetic (seeded config-3 map, targets = renders of a perturbed copy; no dataset)",
             "config": {"workload": f"config 3 window (1M Gaussians, 12 x 1241x376), {iters} mapping iterations per "
                                    "graph replay, alpha = 0.98, lambda_iso = 10 / (3 |G|), first keyframe frozen",
-                       "l2": "flushed (256 MB write) before every replay", "graph": True},
+                       "l2": "flushed (256 MB write) before every replay", "graph": True, "schedule": sched},
             "views_per_s": V * iters / (ms / 1e3),
             "stages_ms_per_iteration": stage_tot, "stages_timed_in": "eager iterations after the timed region",
             "roofline": {"kernel": "map_adam", "bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]),

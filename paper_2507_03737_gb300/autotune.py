@@ -25,7 +25,7 @@ SEARCH_SPACE = {
     "pixels_per_thread": [1, 2, 4],
     "bwd_pixels_per_thread": [1, 2, 4],
     "batch": [64, 128, 256, 512],
-    "blocks_per_sm": [0, 2, 4, 8],
+    "blocks_per_sm": [0, 2, 4, 8, 16],
 }
 FIELDS = ("tile_w", "tile_h", "pixels_per_thread", "bwd_pixels_per_thread", "batch", "blocks_per_sm")
 

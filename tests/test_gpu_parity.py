@@ -178,7 +178,8 @@ def test_persistent_and_recompute_and_det(R):
                      ("ppt1", dict(pixels_per_thread=1, bwd_pixels_per_thread=1)),
                      ("ppt4_recompute", dict(pixels_per_thread=4, bwd_pixels_per_thread=2, recompute=1)),
                      ("det", dict(deterministic=1)), ("det_recompute", dict(deterministic=1, recompute=1)),
-                     ("det_persistent", dict(deterministic=1, blocks_per_sm=3, batch=64))):
+                     ("det_persistent", dict(deterministic=1, blocks_per_sm=3, batch=64)),
+                     ("persistent16_ppt4", dict(blocks_per_sm=16, bwd_pixels_per_thread=4, batch=64))):
         out = R.render_np(sc, options=_opts(**kw))
         for k in base:
             np.testing.assert_array_equal(out[k], base[k], err_msg=f"{name} {k}")
