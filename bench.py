@@ -36,12 +36,12 @@ FP32_LANES_PER_SM = 128
 # Blend schedules the autotuner found for a workload (autotune.py, coordinate
 # descent on CUDA-event timings), applied by default so that every run times, and
 # the committed ncu summaries profile, the same kernels: config 3 runs a persistent
-# heaviest-first grid of 16 CTAs per SM, 2 pixels per forward and 4 per backward
-# blend thread, batches of 64 staged Gaussians; the small single view of config 1
+# heaviest-first grid of 12 CTAs per SM, 2 pixels per forward and 4 per backward
+# blend thread, batches of 128 staged Gaussians; the small single view of config 1
 # fills the GPU only with 8x8 tiles of one pixel per thread.
 TUNED_SCHEDULES = {
     1: {"tile_w": 8, "tile_h": 8, "pixels_per_thread": 1, "bwd_pixels_per_thread": 1, "batch": 64},
-    3: {"blocks_per_sm": 16, "pixels_per_thread": 2, "bwd_pixels_per_thread": 4, "batch": 64},
+    3: {"blocks_per_sm": 12, "pixels_per_thread": 2, "bwd_pixels_per_thread": 4, "batch": 128},
 }
 # blend schedule of the mapping-iteration row (run_mapping says how it was chosen)
 MAPPING_SCHEDULE = {"blocks_per_sm": 8, "pixels_per_thread": 2, "bwd_pixels_per_thread": 2}

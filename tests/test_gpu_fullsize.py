@@ -97,8 +97,8 @@ def _twist_by_view(twist_crops, crops, n_views):
 
 
 # the library default, and the schedule the autotuner picks for config 3 (a persistent
-# heaviest-first grid of 16 CTAs per SM, 4 pixels per backward thread, batches of 64)
-CONFIG3_SCHEDULES = [None, dict(blocks_per_sm=16, pixels_per_thread=2, bwd_pixels_per_thread=4, batch=64)]
+# heaviest-first grid of 12 CTAs per SM, 4 pixels per backward thread, batches of 128)
+CONFIG3_SCHEDULES = [None, dict(blocks_per_sm=12, pixels_per_thread=2, bwd_pixels_per_thread=4, batch=128)]
 
 
 @pytest.mark.parametrize("schedule", CONFIG3_SCHEDULES, ids=["default", "autotuned"])
