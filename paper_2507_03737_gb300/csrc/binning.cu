@@ -147,10 +147,10 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
             view = (unsigned)v;
             const float x0 = ceilf(__fsub_rn(ra.x, (float)ext.x)), x1 = floorf(__fadd_rn(ra.x, (float)ext.x));
             const float y0 = ceilf(__fsub_rn(ra.y, (float)ext.y)), y1 = floorf(__fadd_rn(ra.y, (float)ext.y));
-            const int tx0 = (x0 > 0.f ? (int)x0 : 0) / vb.tile_w;
-            const int tx1 = (x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1) / vb.tile_w;
-            const int ty0 = (y0 > 0.f ? (int)y0 : 0) / vb.tile_h;
-            const int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
+            const int tx0 = tile_of(x0 > 0.f ? (int)x0 : 0, vb.tile_w);
+            const int tx1 = tile_of(x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1, vb.tile_w);
+            const int ty0 = tile_of(y0 > 0.f ? (int)y0 : 0, vb.tile_h);
+            const int ty1 = tile_of(y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1, vb.tile_h);
             ntx = (unsigned)(tx1 - tx0 + 1);
             cnt = ntx * (unsigned)(ty1 - ty0 + 1);
             t0 = (unsigned)tx0 | ((unsigned)ty0 << 16);

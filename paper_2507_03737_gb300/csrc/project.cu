@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     Activated A;
     bool ok = activate(ls, q, a.opacity_logits[g], A) && live;
+    const float lo2 = log2f(A.opacity);  // per Gaussian, staged with every visible record
     // Degree 0 keeps its colour in registers; higher degrees re-read their SH
     // coefficients (L1-resident) in each view that sees the Gaussian rather
     // than hold 3 (D + 1)^2 registers across the view loop.
@@ -256,10 +257,10 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                 float x0 = ceilf(__fsub_rn(u, (float)rx)), x1 = floorf(__fadd_rn(u, (float)rx));
                 float y0 = ceilf(__fsub_rn(vv, (float)ry)), y1 = floorf(__fadd_rn(vv, (float)ry));
                 if (x1 >= 0.f && x0 <= (float)(vi.w - 1) && y1 >= 0.f && y0 <= (float)(vi.h - 1) && x0 <= x1 && y0 <= y1) {
-                    int tx0 = (x0 > 0.f ? (int)x0 : 0) / vb.tile_w;
-                    int tx1 = (x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1) / vb.tile_w;
-                    int ty0 = (y0 > 0.f ? (int)y0 : 0) / vb.tile_h;
-                    int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
+                    int tx0 = tile_of(x0 > 0.f ? (int)x0 : 0, vb.tile_w);
+                    int tx1 = tile_of(x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1, vb.tile_w);
+                    int ty0 = tile_of(y0 > 0.f ? (int)y0 : 0, vb.tile_h);
+                    int ty1 = tile_of(y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1, vb.tile_h);
                     // colour (Eq. 2; SH for degree >= 1)
                     float col[3];
                     if (D == 0) {
@@ -281,7 +282,6 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                         for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(c3[ch], 0.0f);
                     }
                     Record R;
-                    const float lo2 = log2f(A.opacity);
                     const float qc = fminf(kCutoffQ, 2.0f * kLn2 * (lo2 - kSkipL)) * (1.0f + 2e-5f + 8e-7f * kappa);
                     R.a = make_float4(u, vv, cc * idet, -cb * idet);
                     R.b = make_float4(ca * idet, A.opacity, pz, lo2);

@@ -50,10 +50,10 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
     float z = a.rec[r].b.z;
     float x0 = ceilf(__fsub_rn(ra.x, (float)ext.x)), x1 = floorf(__fadd_rn(ra.x, (float)ext.x));
     float y0 = ceilf(__fsub_rn(ra.y, (float)ext.y)), y1 = floorf(__fadd_rn(ra.y, (float)ext.y));
-    int tx0 = (x0 > 0.f ? (int)x0 : 0) / vb.tile_w;
-    int tx1 = (x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1) / vb.tile_w;
-    int ty0 = (y0 > 0.f ? (int)y0 : 0) / vb.tile_h;
-    int ty1 = (y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1) / vb.tile_h;
+    int tx0 = tile_of(x0 > 0.f ? (int)x0 : 0, vb.tile_w);
+    int tx1 = tile_of(x1 < (float)(vi.w - 1) ? (int)x1 : vi.w - 1, vb.tile_w);
+    int ty0 = tile_of(y0 > 0.f ? (int)y0 : 0, vb.tile_h);
+    int ty1 = tile_of(y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1, vb.tile_h);
     const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | g;
     float acc[kGrad2d];
 #pragma unroll

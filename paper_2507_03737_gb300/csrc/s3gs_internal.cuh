@@ -50,6 +50,9 @@ __device__ __forceinline__ unsigned div_small(unsigned x, unsigned d, unsigned &
     }
     return q;
 }
+// Tile index of a non-negative pixel coordinate. Every supported tile side (8,
+// 16 or 32) is a power of two, so the quotient is a shift.
+__device__ __forceinline__ int tile_of(int x, int side) { return x >> (__ffs(side) - 1); }
 __device__ __forceinline__ int depth_bin(float z) {
     const int b = (int)(__float_as_uint(z) >> 19) - 1993;
     return b < 0 ? 0 : (b > kDepthBins - 1 ? kDepthBins - 1 : b);
