@@ -79,7 +79,7 @@ __device__ __forceinline__ void stage(const BlendArgs &a, long long rbase, unsig
         const Record r = a.rec[rbase + g];
         const StagedGauss sg = stage_record(r);
         s_p0[k] = make_float4(sg.u, sg.v, sg.a, sg.b);
-        s_p1[k] = make_float4(sg.c, sg.lo2, sg.o, sg.z);
+        s_p1[k] = make_float4(sg.c, sg.lo2, sg.thr, sg.z);
         if (s_col) s_col[k] = r.c;
         if (s_g) s_g[k] = g;
     }
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     if (done[p]) continue;
-                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, p1.x, p1.y);
+                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z);
                     if (COUNT) ++n_proc;
                     if (!pe.pass) continue;
                     const float al = pair_alpha(pe);
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         if (done[p]) continue;
-                        const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y);
+                        const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y, q1.z);
                         if (!pe.pass) continue;
                         const float Tn = next_T(T[p], pair_alpha(pe));
                         if (Tn < kTMin) {
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     if (pos >= last[p]) continue;
-                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y);
+                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y, q1.z);
                     if (COUNT) ++n_proc;
                     if (!pe.pass) continue;
                     contrib = true;

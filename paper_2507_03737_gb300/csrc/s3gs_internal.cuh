@@ -179,8 +179,8 @@ constexpr float kSkipL = -7.9943534368588578f;  // log2(1/255)
 constexpr float kClampL = -0.0144995696951151f; // log2(0.99)
 
 struct StagedGauss {
-    float u, v, a, b;   // centre, scaled conic (xx, 2 xy)
-    float c, lo2, o, z;  // scaled conic (yy), log2 opacity, opacity, depth
+    float u, v, a, b;      // centre, scaled conic (xx, 2 xy)
+    float c, lo2, thr, z;  // scaled conic (yy), log2 opacity, pass threshold on p, depth
 };
 
 __device__ __forceinline__ StagedGauss stage_record(const Record &r) {
@@ -190,9 +190,11 @@ __device__ __forceinline__ StagedGauss stage_record(const Record &r) {
     g.a = __fmul_rn(-0.5f * kLog2e, r.a.z);
     g.b = __fmul_rn(-kLog2e, r.a.w);
     g.c = __fmul_rn(-0.5f * kLog2e, r.b.x);
-    g.o = r.b.y;
     g.z = r.b.z;
     g.lo2 = r.b.w;
+    // a pair passes when p >= kCutP (inside the 3-sigma ellipse) and p + log2 o >=
+    // log2(1/255) (alpha not skipped): one compare against the larger bound
+    g.thr = fmaxf(kCutP, __fsub_rn(kSkipL, g.lo2));
     return g;
 }
 
@@ -204,20 +206,21 @@ struct PairEval {
 };
 
 __device__ __forceinline__ PairEval eval_pair(float px, float py, float u, float v, float a, float b, float c,
-                                              float lo2) {
+                                              float lo2, float thr) {
     PairEval e;
     e.dx = __fsub_rn(px, u);
     e.dy = __fsub_rn(py, v);
     const float t = __fmaf_rn(a, e.dx, __fmul_rn(b, e.dy));
     const float p = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(c, e.dy), e.dy));
     e.l = __fadd_rn(p, lo2);
-    e.pass = (p >= kCutP) && (e.l >= kSkipL);
+    e.pass = p >= thr;
     e.clamped = e.l >= kClampL;
     return e;
 }
 
 // 2^x with the hardware approximation (relative error below 2^-22); every
-// exponent reaching it lies in [log2(1/255), log2(0.99)], far from denormals.
+// exponent reaching it lies in [log2(1/255), log2(0.99)] (to within the rounding
+// of the pass threshold), far from denormals.
 __device__ __forceinline__ float fast_exp2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
