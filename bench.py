@@ -581,9 +581,21 @@ def run_native(args):
     n_rec = sc.n * wl.V
     nc = (sc.sh_degree + 1) ** 2
     p_in = 4 * (3 + 3 + 4 + 1 + 3 * nc)
-    vis_frac = None
-    bytes_ = {"project": sc.n * p_in + n_rec * 8 + 0.25 * n_rec * 48, "emit": n_rec * 8 + K * 12,
-              "tile_sort": K * 16, "project_bwd": sc.n * p_in * 2 + 0.25 * n_rec * 40 * 2}
+    # visible (Gaussian, view) records of the last forward: the diagonal of the
+    # covisibility counts (outside the timed region)
+    wl.step_batched()  # the state's last forward is the whole window again (not a per-view one)
+    vis_counts = torch.zeros((wl.V, wl.V), dtype=torch.int64, device=device)
+    B.s3gs_covisibility(R.ctx, R.state, vis_counts)
+    n_vis = int(torch.diagonal(vis_counts).sum().item())
+    # algorithmic bytes per launch: parameters read once per call, an 8-byte extent per
+    # record, a 48-byte record per visible record, 8-byte keys (+ 4-byte cursor atomics)
+    # per duplicate, the sort reading the emission buffer twice and writing the list
+    # once, the projection backward reading the parameters and writing their gradients
+    # and reading + clearing a 40-byte gradient row per visible record
+    bytes_ = {"project": sc.n * p_in + n_rec * 8 + n_vis * 48 + sc.n * 4,
+              "emit": n_rec * 8 + n_vis * 48 + K * 12,
+              "tile_sort": K * 24,
+              "project_bwd": sc.n * p_in * 2 + n_vis * 40 * 2 + sc.n * 4}
     dominant = max(stages, key=stages.get) if stages else "blend_bwd"
     ms_dom = stages.get(dominant)
     roof = None
@@ -604,6 +616,20 @@ def run_native(args):
             roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "traffic": None, "ms_per_launch": ms_dom}
         roof["peak_of"] = peak_src
+    # every timed kernel against its own roofline (live CUDA-event stage times)
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    kernels = {}
+    for k, ms in stages.items():
+        if not ms:
+            continue
+        if k in flops:
+            a_ = flops[k] / (ms / 1e3) / 1e12
+            kernels[k] = {"bound": "alu", "achieved": a_, "unit": "TFLOP/s", "frac": a_ / alu_peak,
+                          "flops_per_launch": flops[k], "ms": ms}
+        elif k in bytes_:
+            a_ = bytes_[k] / (ms / 1e3) / 1e9
+            kernels[k] = {"bound": "hbm", "achieved": a_, "unit": "GB/s", "frac": a_ / float(peaks["hbm_gbs"]),
+                          "bytes_per_launch": bytes_[k], "ms": ms}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -631,7 +657,7 @@ def run_native(args):
                 "pairs": {"fwd_processed": fwd_proc, "fwd_blended": fwd_blend, "bwd_processed": bwd_proc,
                           "pairs_per_s_fwd_bwd": (fwd_proc + bwd_proc) * world / (ms_per_step / 1e3),
                           "blended_pairs_per_s": fwd_blend * world / (ms_per_step / 1e3)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "kernels": kernels, "visible_records": n_vis, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps * (2 if staged is not None else 1), "clocks": clk,
                 "wall_s_timed_region": wall,
                 "paper_context": "paper reports only whole-SLAM runtimes (~5 min KITTI-07 on an RTX A6000)"}
