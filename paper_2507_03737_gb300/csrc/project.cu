@@ -143,6 +143,34 @@ __device__ __forceinline__ void cam_centre(const float T[12], float c[3]) {
     for (int i = 0; i < 3; ++i) c[i] = -(T[i] * T[3] + T[4 + i] * T[7] + T[8 + i] * T[11]);
 }
 
+// One coordinate of the view transform, r . m + t, to about one rounding of the
+// result. A mean tens of metres from the world origin seen by a camera a metre
+// away makes the terms cancel: plain FP32 leaves an error near ulp(|m|), which
+// the projection magnifies by f / z (milli-pixels for near Gaussians on a long
+// trajectory, enough to flip a 1/255-skip decision against the FP64 reference).
+// Each product is split exactly with an FMA (p + e = r m) and the sum is a
+// chain of error-free two-sums whose errors are accumulated and added once
+// (compensated dot product, Ogita, Rump and Oishi 2005, "Dot2").
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float view_coord(const float *r, const float m[3], float t) {
+    const float p0 = __fmul_rn(r[0], m[0]), e0 = __fmaf_rn(r[0], m[0], -p0);
+    const float p1 = __fmul_rn(r[1], m[1]), e1 = __fmaf_rn(r[1], m[1], -p1);
+    const float p2 = __fmul_rn(r[2], m[2]), e2 = __fmaf_rn(r[2], m[2], -p2);
+    float s, e, c;
+    two_sum(p0, p1, s, e);
+    c = __fadd_rn(__fadd_rn(e0, e1), e);
+    two_sum(s, p2, s, e);
+    c = __fadd_rn(c, __fadd_rn(e2, e));
+    two_sum(s, t, s, e);
+    c = __fadd_rn(c, e);
+    return __fadd_rn(s, c);
+}
+
 // Counts the (tile, depth bin) buckets of the 32 records a warp has just made
 // for one view: an inclusive warp scan numbers the records' candidate tiles
 // (their bounding rectangles), and in each round every lane takes one
@@ -225,9 +253,9 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
         int ctx0 = 0, cty0 = 0, cntx = 0, cnty = 0, cbin = 0;
         float T[12];
         load_pose(vi, a.Tdev, v, T);
-        float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
-        float py = T[4] * m[0] + T[5] * m[1] + T[6] * m[2] + T[7];
-        float pz = T[8] * m[0] + T[9] * m[1] + T[10] * m[2] + T[11];
+        float px = view_coord(T, m, T[3]);
+        float py = view_coord(T + 4, m, T[7]);
+        float pz = view_coord(T + 8, m, T[11]);
         const bool in_cone = a.guard <= 0.f || (fabsf(px) <= a.guard * pz && fabsf(py) <= a.guard * pz);
         if (ok && pz > a.near_z && in_cone) {
             float Sc[9];
@@ -380,9 +408,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
                 const float *gr = gr4[u];
                 float T[12];
                 load_pose(vi, a.Tdev, v, T);
-                float px = T[0] * m[0] + T[1] * m[1] + T[2] * m[2] + T[3];
-                float py = T[4] * m[0] + T[5] * m[1] + T[6] * m[2] + T[7];
-                float pz = T[8] * m[0] + T[9] * m[1] + T[10] * m[2] + T[11];
+                float px = view_coord(T, m, T[3]);
+                float py = view_coord(T + 4, m, T[7]);
+                float pz = view_coord(T + 8, m, T[11]);
                 float Sc[9];
                 cam_cov(T, A.Sig, Sc);
                 float iz = 1.0f / pz, iz2 = iz * iz;

@@ -1,4 +1,7 @@
 """Shared helpers of the GPU parity tests (tolerances and comparisons)."""
+import json
+import os
+
 import numpy as np
 
 # Tolerances of the parity bar: <= 1e-4 absolute on rgb and alpha, <= 1e-4
@@ -8,7 +11,19 @@ TOL_ABS = 1e-4
 TOL_REL = 1e-4
 TOL_FLOOR = 1e-6
 TOL_GRAD = 1e-3
-MARGIN = 1e-4  # pixels whose FP64 decisions sit closer than this to a threshold are excluded
+MARGIN = 1e-5  # pixels whose FP64 decisions sit closer than this (relative) to a threshold are excluded
+
+
+def report(name, res):
+    """Record a parity comparison's exclusion counts: printed (pytest -s shows it) and,
+    when S3GS_PARITY_LOG names a file, appended to it as one JSON line."""
+    line = {"test": name, **{k: v for k, v in res.items() if isinstance(v, (int, float, str))}}
+    print("PARITY " + json.dumps(line))
+    path = os.environ.get("S3GS_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(line) + "\n")
+    return res
 
 
 def expand3(x, cameras):
@@ -35,30 +50,68 @@ def pixel_mask(ref, thresh=MARGIN):
     return ref["margin"] > thresh
 
 
+def _pixel_fails(gpu, ref, cameras, sel):
+    """Per pixel: does any output of the pixel exceed the parity tolerance? (sel: bool [P])"""
+    bad = np.zeros(sel.size, bool)
+    off = 0
+    for c in cameras:
+        hw = c["width"] * c["height"]
+        s1 = slice(off, off + hw)
+        for k, ch in (("rgb", 3), ("pointmap", 3), ("depth", 1), ("alpha", 1)):
+            if k not in gpu or k not in ref:
+                continue
+            a = gpu[k][ch * off: ch * (off + hw)].reshape(ch, hw).astype(np.float64)
+            b = ref[k][ch * off: ch * (off + hw)].reshape(ch, hw)
+            if k in ("rgb", "alpha"):
+                e = np.abs(a - b) > TOL_ABS
+            else:
+                e = np.abs(a - b) > TOL_REL * np.abs(b) + TOL_FLOOR
+            bad[s1] |= e.any(axis=0)
+        off += hw
+    return bad & sel
+
+
 def compare_forward(gpu, ref, cameras, mask=None, keys=("rgb", "depth", "pointmap", "alpha"),
-                    max_excluded=0.01):
+                    max_excluded=0.002, name=None):
+    """Forward outputs against the oracle on the pixels whose decisions lie outside the
+    margin band; at most max(3, max_excluded * pixels) pixels may be excluded. The
+    result also counts, for the record, the pixels a band ten times narrower would add
+    and how many of those would break the tolerance; it is reported (see report)
+    under ``name``, by default the running test's id."""
     m = pixel_mask(ref) if mask is None else mask
     m3 = expand3(m, cameras)
     P = m.size
-    res = {"excluded": int((~m).sum()), "pixels": P}
+    res = {"excluded": int((~m).sum()), "pixels": P, "max_excluded": int(max(3, max_excluded * P))}
+    if mask is None and "margin" in ref:
+        narrow = (ref["margin"] > MARGIN / 10) & ~m
+        res["narrow_band_added"] = int(narrow.sum())
+        res["narrow_band_fail"] = int(_pixel_fails(gpu, ref, cameras, narrow).sum())
+    worst = {}
     if "rgb" in keys:
         res["rgb"] = float(np.abs(gpu["rgb"][m3] - ref["rgb"][m3]).max(initial=0))
-        assert res["rgb"] <= TOL_ABS, res
     if "alpha" in keys:
         res["alpha"] = float(np.abs(gpu["alpha"][m] - ref["alpha"][m]).max(initial=0))
-        assert res["alpha"] <= TOL_ABS, res
     if "depth" in keys:
         a, b = gpu["depth"][m], ref["depth"][m]
         bad = np.abs(a - b) > TOL_REL * np.abs(b) + TOL_FLOOR
         res["depth_bad"] = int(bad.sum())
         res["depth_rel"] = float((np.abs(a - b) / (np.abs(b) + 1e-3)).max(initial=0))
-        assert res["depth_bad"] == 0, (res, _worst(a, b))
+        if bad.any():
+            worst["depth"] = _worst(a, b)
     if "pointmap" in keys:
         a, b = gpu["pointmap"][m3], ref["pointmap"][m3]
         bad = np.abs(a - b) > TOL_REL * np.abs(b) + TOL_FLOOR
         res["pointmap_bad"] = int(bad.sum())
-        assert res["pointmap_bad"] == 0, (res, _worst(a, b))
-    assert res["excluded"] <= max(3, max_excluded * P), res
+        if bad.any():
+            worst["pointmap"] = _worst(a, b)
+    if name is None:
+        name = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    report(name, res)
+    assert res.get("rgb", 0.0) <= TOL_ABS, res
+    assert res.get("alpha", 0.0) <= TOL_ABS, res
+    assert res.get("depth_bad", 0) == 0, (res, worst)
+    assert res.get("pointmap_bad", 0) == 0, (res, worst)
+    assert res["excluded"] <= res["max_excluded"], res
     return res
 
 
