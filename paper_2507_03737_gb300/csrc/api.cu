@@ -76,7 +76,7 @@ struct s3gs_state {
     DevBuf<float> T_final;
     DevBuf<unsigned> n_last;
     DevBuf<float> twist_part;
-    DevBuf<float> loss_part;  // fused-loss backward: one partial per blend CTA
+    DevBuf<float> loss_part;  // fused-loss backward: one partial per tile
     unsigned *bucket = nullptr;
     DevCounters *ctr = nullptr;
     DevCounters *ctr_host = nullptr;  // pinned
@@ -621,7 +621,7 @@ s3gs_status render_bwd_impl(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
     }
     if (l1 && loss_device) {
         StageTimer tm(ctx, kStLoss, s);
-        CK(launch_loss_final(st->loss_part.p, (int)grid, loss_device, s), "loss_final");
+        CK(launch_loss_final(st->loss_part.p, (int)T, loss_device, s), "loss_final");
     }
 
     if (det) {

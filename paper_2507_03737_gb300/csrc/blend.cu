@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
     extern __shared__ float4 smem[];
     __shared__ int s_tile;
     __shared__ unsigned s_maxlast;
+    __shared__ float s_loss[NW];
     const unsigned B = (unsigned)a.batch;
     float4 *s_p0 = smem;
     float4 *s_p1 = smem + B;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (a.ctr->overflow) return;
     unsigned long long n_proc = 0;
-    float loss_acc = 0.f;  // fused L1 loss of this thread's pixels
+    float loss_acc = 0.f;  // fused L1 loss of this thread's pixels in the current tile
     for (int iter = 0;; ++iter) {
         const int t = next_tile(a, vb, &a.ctr->work_bwd, iter, &s_tile);
         if (t < 0) break;
@@ -392,8 +393,21 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
         }
 
         if (threadIdx.x == 0) s_maxlast = 0;
+        if (a.l1) {
+            // this tile's loss: warps summed in a fixed order, one partial per tile, so
+            // the loss does not depend on which CTA of a persistent grid took the tile
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+            if (lane == 0) s_loss[warp] = loss_acc;
+            loss_acc = 0.f;
+        }
         __syncthreads();
         if (mylast) atomicMax(&s_maxlast, mylast);
+        if (a.l1 && threadIdx.x == 0) {
+            float x = 0.f;
+            for (int w = 0; w < NW; ++w) x += s_loss[w];
+            a.loss_partial[t] = x;
+        }
         __syncthreads();
         const unsigned maxlast = s_maxlast;
         const unsigned wmaxlast = __reduce_max_sync(0xffffffffu, mylast);  // this warp's last list entry
@@ -499,19 +513,6 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
         }
     }
     if (COUNT) atomicAdd(&a.ctr->bwd_processed, n_proc);
-    if (a.l1) {
-        // this CTA's loss partial, warps summed in a fixed order
-        __shared__ float s_loss[NW];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
-        if (lane == 0) s_loss[warp] = loss_acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float x = 0.f;
-            for (int w = 0; w < NW; ++w) x += s_loss[w];
-            a.loss_partial[blockIdx.x] = x;
-        }
-    }
 }
 
 size_t fwd_smem(int batch) { return (size_t)batch * (3 * sizeof(float4)); }

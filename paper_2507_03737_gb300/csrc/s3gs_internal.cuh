@@ -309,12 +309,12 @@ struct BlendArgs {
     int geom_only;      // backward: only the geometry slots (u, v, conic, z) are needed
     // backward with the L1 mapping loss fused in (l1 != 0): the upstream gradients
     // are formed per pixel from the forward's outputs and the targets instead of
-    // being read, and each CTA writes its share of the loss to loss_partial
+    // being read, and the loss of each tile goes to loss_partial[tile]
     int l1;
     const float *o_rgb, *o_depth, *o_pointmap;  // the forward's outputs
     const float *t_rgb, *t_depth, *t_pointmap, *mask;
     float kr, kd, kg;                           // w_rgb / (3 P), w_depth / P, w_geo / (3 P)
-    float *loss_partial;                        // [gridDim.x]
+    float *loss_partial;                        // [total tiles]: the loss of each tile
 };
 cudaError_t launch_blend_fwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
 cudaError_t launch_blend_bwd(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s);
