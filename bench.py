@@ -816,12 +816,30 @@ POSE_METRIC = ("pose refinement iterations/s (render + L1 loss + pose-only backw
                "1M Gaussians, one 1241×376 frame")
 
 
-def pose_workload(sc):
-    """View 0 of the config-3 window, started 3 cm / 1.4 degrees off its true pose."""
+POSE_START_TWIST = [0.02, -0.015, 0.015, 0.012, -0.015, 0.01]
+
+
+def pose_workload(sc, reference=False):
+    """View 0 of the config-3 window, started 3 cm / 1.4 degrees off its true pose:
+    T_start = Exp(tau) T_true. The native arm evaluates Exp with the library's own
+    kernel; the reference arm (CPU only) with the oracle's."""
     import numpy as np
-    from paper_2507_03737_gb300.autograd import apply_twist
     cam = sc.cameras[0]
-    start = apply_twist(np.asarray(cam["T_cw"], np.float64), [0.02, -0.015, 0.015, 0.012, -0.015, 0.01])
+    if reference:
+        from oracle import pose_oracle as PO
+        E = PO.se3_exp(POSE_START_TWIST)
+    else:
+        import torch
+        from paper_2507_03737_gb300 import binding as B
+        ctx = B.s3gs_create(torch.cuda.current_device())
+        tau = torch.tensor([POSE_START_TWIST], dtype=torch.float32, device="cuda")
+        E = torch.empty((1, 12), dtype=torch.float32, device="cuda")
+        B.s3gs_se3_exp(ctx, 1, tau, E)
+        torch.cuda.synchronize()
+        B.s3gs_destroy(ctx)
+        E = E.cpu().numpy().astype(np.float64).reshape(3, 4)
+    T = np.asarray(cam["T_cw"], np.float64).reshape(3, 4)
+    start = np.concatenate([E[:, :3] @ T[:, :3], (E[:, :3] @ T[:, 3] + E[:, 3])[:, None]], axis=1)
     return cam, dict(cam, T_cw=np.asarray(start, np.float32))
 
 
@@ -838,10 +856,11 @@ def run_pose(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0  # tracking one frame runs on one GPU; other ranks have no work
     sc = scenes.config_scene(3)
-    true_cam, start_cam = pose_workload(sc)
     if args.impl == "reference":
+        true_cam, start_cam = pose_workload(sc, reference=True)
         return run_pose_reference(args, sc, true_cam, start_cam)
     torch.cuda.set_device(local)
+    true_cam, start_cam = pose_workload(sc)
     tw, th = tile_shape(args.tile)
     opt = B.s3gs_options_default(tile_w=tw, tile_h=th, blocks_per_sm=args.blocks_per_sm,
                                  deterministic=args.deterministic, recompute=max(args.recompute, 0))

@@ -8,7 +8,6 @@ which is what a pose-refinement step needs.
 """
 from __future__ import annotations
 
-import math
 import weakref
 
 import numpy as np
@@ -16,7 +15,7 @@ import torch
 
 from . import binding as B
 
-__all__ = ["Renderer", "RenderFunction", "render", "se3_exp", "apply_twist", "OUTPUTS"]
+__all__ = ["Renderer", "RenderFunction", "render", "OUTPUTS"]
 
 OUTPUTS = ("rgb", "depth", "pointmap", "alpha")
 PARAMS = ("means", "log_scales", "quats", "opacity_logits", "colors")
@@ -173,29 +172,3 @@ def render(renderer: Renderer, params: dict, cameras, twist=None, options=None):
                                 params["opacity_logits"], params["colors"], twist, renderer, cameras,
                                 params["sh_degree"], options)
 
-
-def se3_exp(tau) -> np.ndarray:
-    """Exp of a twist (rho, phi) as a 3x4 [R | V rho] (Rodrigues)."""
-    tau = np.asarray(tau, np.float64)
-    rho, phi = tau[:3], tau[3:]
-    th = float(np.linalg.norm(phi))
-    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
-    if th < 1e-9:
-        R = np.eye(3) + K
-        V = np.eye(3) + 0.5 * K
-    else:
-        a = math.sin(th) / th
-        b = (1 - math.cos(th)) / th ** 2
-        c = (th - math.sin(th)) / th ** 3
-        R = np.eye(3) + a * K + b * K @ K
-        V = np.eye(3) + b * K + c * K @ K
-    return np.concatenate([R, (V @ rho)[:, None]], 1)
-
-
-def apply_twist(T_cw, tau) -> np.ndarray:
-    """Exp(tau) * T_cw for a 3x4 world-to-camera pose (left perturbation, Eq. 9)."""
-    E = se3_exp(tau)
-    T = np.asarray(T_cw, np.float64).reshape(3, 4)
-    R = E[:, :3] @ T[:, :3]
-    t = E[:, :3] @ T[:, 3] + E[:, 3]
-    return np.concatenate([R, t[:, None]], 1)
