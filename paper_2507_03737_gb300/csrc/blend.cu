@@ -175,13 +175,14 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
         const long long rbase = (long long)c.v * a.n;
         const float px = (float)c.i;
         const unsigned s = a.tile_start[t * kDepthBins], e = a.tile_start[(t + 1) * kDepthBins];
-        float T[P], C0[P], C1[P], C2[P], D[P];
+        float T[P], C0[P], C1[P], C2[P], D[P], py[P];
         unsigned last[P];
         bool done[P];
         bool all_done = true;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             T[p] = 1.f; C0[p] = C1[p] = C2[p] = D[p] = 0.f; last[p] = 0;
+            py[p] = (float)c.j[p];
             done[p] = !c.inside[p];
             all_done = all_done && done[p];
         }
@@ -193,26 +194,60 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
             for (unsigned k = 0; k < cnt && !all_done; ++k) {
                 const float4 p0 = s_p0[k], p1 = s_p1[k], col = s_col[k];
                 const unsigned idx = b - s + k + 1;
+                if constexpr (P % 2 == 0) {
+                    // the quadratic form of two pixels of the column at once (packed FP32,
+                    // each lane rounding as eval_pair does); the rest per pixel
+                    const float dx = __fsub_rn(px, p0.x);
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    if (done[p]) continue;
-                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z);
-                    if (COUNT) ++n_proc;
-                    if (!pe.pass) continue;
-                    const float al = pair_alpha(pe);
-                    const float Tn = next_T(T[p], al);
-                    if (Tn < kTMin) {
-                        done[p] = true;
-                        continue;
+                    for (int h = 0; h < P / 2; ++h) {
+                        if (done[2 * h] && done[2 * h + 1]) continue;
+                        float2 dy, pp, ll;
+                        eval_pair2(dx, make_float2(py[2 * h], py[2 * h + 1]), p0.y, p0.z, p0.w, p1.x, p1.y, dy, pp, ll);
+#pragma unroll
+                        for (int e2 = 0; e2 < 2; ++e2) {
+                            const int p = 2 * h + e2;
+                            if (done[p]) continue;
+                            if (COUNT) ++n_proc;
+                            const float pe = e2 ? pp.y : pp.x, le = e2 ? ll.y : ll.x;
+                            if (!(pe >= p1.z)) continue;  // outside the 3-sigma ellipse or below 1/255
+                            const float al = le >= kClampL ? kAlphaMax : fast_exp2(le);
+                            const float Tn = next_T(T[p], al);
+                            if (Tn < kTMin) {
+                                done[p] = true;
+                                continue;
+                            }
+                            const float w = al * T[p];
+                            C0[p] = fmaf(col.x, w, C0[p]);
+                            C1[p] = fmaf(col.y, w, C1[p]);
+                            C2[p] = fmaf(col.z, w, C2[p]);
+                            D[p] = fmaf(p1.w, w, D[p]);
+                            T[p] = Tn;
+                            last[p] = idx;
+                            if (COUNT) ++n_blend;
+                        }
                     }
-                    const float w = al * T[p];
-                    C0[p] = fmaf(col.x, w, C0[p]);
-                    C1[p] = fmaf(col.y, w, C1[p]);
-                    C2[p] = fmaf(col.z, w, C2[p]);
-                    D[p] = fmaf(p1.w, w, D[p]);
-                    T[p] = Tn;
-                    last[p] = idx;
-                    if (COUNT) ++n_blend;
+                } else {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        if (done[p]) continue;
+                        const PairEval pe = eval_pair(px, py[p], p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z);
+                        if (COUNT) ++n_proc;
+                        if (!pe.pass) continue;
+                        const float al = pair_alpha(pe);
+                        const float Tn = next_T(T[p], al);
+                        if (Tn < kTMin) {
+                            done[p] = true;
+                            continue;
+                        }
+                        const float w = al * T[p];
+                        C0[p] = fmaf(col.x, w, C0[p]);
+                        C1[p] = fmaf(col.y, w, C1[p]);
+                        C2[p] = fmaf(col.z, w, C2[p]);
+                        D[p] = fmaf(p1.w, w, D[p]);
+                        T[p] = Tn;
+                        last[p] = idx;
+                        if (COUNT) ++n_blend;
+                    }
                 }
                 all_done = true;
 #pragma unroll
@@ -279,12 +314,13 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
         const unsigned s = a.tile_start[t * kDepthBins], e = a.tile_start[(t + 1) * kDepthBins];
 
         // per-pixel blend state: stored by the forward, or replayed here
-        float T[P];
+        float T[P], py[P];
         unsigned last[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             T[p] = 1.f;
             last[p] = 0;
+            py[p] = (float)c.j[p];
         }
         if (RECOMPUTE) {
             bool done[P];
@@ -301,18 +337,45 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                 __syncthreads();
                 for (unsigned k = 0; k < cnt && !all_done; ++k) {
                     const float4 p0 = s_p0[k], q1 = s_p1[k];
+                    const unsigned idx = b - s + k + 1;
+                    if constexpr (P % 2 == 0) {
+                        // the forward's evaluation (packed quadratic form, per-pixel decisions),
+                        // T and the last index only
+                        const float dx = __fsub_rn(px, p0.x);
 #pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        if (done[p]) continue;
-                        const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y, q1.z);
-                        if (!pe.pass) continue;
-                        const float Tn = next_T(T[p], pair_alpha(pe));
-                        if (Tn < kTMin) {
-                            done[p] = true;
-                            continue;
+                        for (int h = 0; h < P / 2; ++h) {
+                            if (done[2 * h] && done[2 * h + 1]) continue;
+                            float2 dy, pp, ll;
+                            eval_pair2(dx, make_float2(py[2 * h], py[2 * h + 1]), p0.y, p0.z, p0.w, q1.x, q1.y, dy, pp, ll);
+#pragma unroll
+                            for (int e2 = 0; e2 < 2; ++e2) {
+                                const int p = 2 * h + e2;
+                                if (done[p]) continue;
+                                const float pe = e2 ? pp.y : pp.x, le = e2 ? ll.y : ll.x;
+                                if (!(pe >= q1.z)) continue;
+                                const float Tn = next_T(T[p], le >= kClampL ? kAlphaMax : fast_exp2(le));
+                                if (Tn < kTMin) {
+                                    done[p] = true;
+                                    continue;
+                                }
+                                T[p] = Tn;
+                                last[p] = idx;
+                            }
                         }
-                        T[p] = Tn;
-                        last[p] = b - s + k + 1;
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            if (done[p]) continue;
+                            const PairEval pe = eval_pair(px, py[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y, q1.z);
+                            if (!pe.pass) continue;
+                            const float Tn = next_T(T[p], pair_alpha(pe));
+                            if (Tn < kTMin) {
+                                done[p] = true;
+                                continue;
+                            }
+                            T[p] = Tn;
+                            last[p] = idx;
+                        }
                     }
                     all_done = true;
 #pragma unroll
@@ -436,10 +499,84 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                 for (int q = 0; q < kGrad2d; ++q) vals[q] = 0.f;
                 bool contrib = false;
                 const float4 p0 = s_p0[k], q1 = s_p1[k];
+                if constexpr (P % 2 == 0) {
+                    // pixels in pairs of adjacent rows, branch-free in packed FP32: a pixel
+                    // the Gaussian does not reach (beyond its last contributor, outside the
+                    // cutoff or skipped) takes the arithmetic with alpha = 0, which leaves its
+                    // T, its behind-value and every sum exactly unchanged; the quadratic form
+                    // and the decisions round as the scalar path below does. The pair sums
+                    // are per lane (even rows, odd rows) and added before the warp reduction.
+                    // A thread's pixels share their column, hence dx: the moments carrying
+                    // dx are sum g dx = dx S, sum g dx^2 = dx (dx S) and sum g dx dy = dx Y
+                    // (S = sum g, Y = sum g dy), so per pair only S, Y and sum g dy^2 are
+                    // accumulated.
+                    const float4 col = s_col[k];
+                    const float dx = __fsub_rn(px, p0.x);
+                    float2 v2[kGrad2d];
+#pragma unroll
+                    for (int q = 0; q < kGrad2d; ++q) v2[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int h = 0; h < P / 2; ++h) {
+                        const int r0 = 2 * h, r1 = 2 * h + 1;
+                        if (pos >= last[r0] && pos >= last[r1]) continue;
+                        float2 dy, pp, ll;
+                        eval_pair2(dx, make_float2(py[r0], py[r1]), p0.y, p0.z, p0.w, q1.x, q1.y, dy, pp, ll);
+                        const bool c0 = pos < last[r0] && pp.x >= q1.z, c1 = pos < last[r1] && pp.y >= q1.z;
+                        if (COUNT) n_proc += (unsigned long long)(pos < last[r0]) + (unsigned long long)(pos < last[r1]);
+                        if (!(c0 || c1)) continue;  // neither pixel passes the cutoff and skip
+                        contrib = true;
+                        const bool k0 = ll.x >= kClampL, k1 = ll.y >= kClampL;
+                        const float a0 = c0 ? (k0 ? kAlphaMax : fast_exp2(ll.x)) : 0.f;
+                        const float a1 = c1 ? (k1 ? kAlphaMax : fast_exp2(ll.y)) : 0.f;
+                        const float2 al = make_float2(a0, a1);
+                        const float2 om = __fadd2_rn(bcast2(1.f), make_float2(-a0, -a1));
+                        const float2 Tp = make_float2(T[r0], T[r1]);
+                        // T in front of this Gaussian (alpha = 0: T / 1)
+                        const float2 Tk = make_float2(c0 ? __fdividef(Tp.x, om.x) : Tp.x, c1 ? __fdividef(Tp.y, om.y) : Tp.y);
+                        const float2 w = __fmul2_rn(al, Tk);
+                        const float2 g0 = make_float2(gC0[r0], gC0[r1]), g1 = make_float2(gC1[r0], gC1[r1]);
+                        const float2 g2 = make_float2(gC2[r0], gC2[r1]), gd = make_float2(gD[r0], gD[r1]);
+                        const float2 f = __ffma2_rn(bcast2(col.x), g0, __ffma2_rn(bcast2(col.y), g1,
+                                                    __ffma2_rn(bcast2(col.z), g2, __fmul2_rn(bcast2(q1.w), gd))));
+                        const float2 Bp = make_float2(Bacc[r0], Bacc[r1]);
+                        const float2 fb = __fadd2_rn(f, make_float2(-Bp.x, -Bp.y));  // f - B
+                        const float2 da = __fmul2_rn(Tk, fb);
+                        // the value behind the next Gaussian: alpha f + (1 - alpha) B = B + alpha (f - B)
+                        const float2 Bn = __ffma2_rn(al, fb, Bp);
+                        Bacc[r0] = Bn.x; Bacc[r1] = Bn.y;
+                        T[r0] = Tk.x; T[r1] = Tk.y;
+                        if (!GEOM) {
+                            v2[kGR] = __ffma2_rn(w, g0, v2[kGR]);
+                            v2[kGG] = __ffma2_rn(w, g1, v2[kGG]);
+                            v2[kGBl] = __ffma2_rn(w, g2, v2[kGBl]);
+                        }
+                        v2[kGZ] = __ffma2_rn(w, gd, v2[kGZ]);
+                        // g = dL/dalpha * alpha (zero where alpha is clamped): S, Y, sum g dy^2
+                        const float2 g = __fmul2_rn(da, make_float2(k0 ? 0.f : a0, k1 ? 0.f : a1));
+                        const float2 gy = __fmul2_rn(g, dy);
+                        v2[kGO] = __fadd2_rn(v2[kGO], g);
+                        v2[kGV] = __fadd2_rn(v2[kGV], gy);
+                        v2[kGC] = __ffma2_rn(gy, dy, v2[kGC]);
+                    }
+                    const float S = __fadd_rn(v2[kGO].x, v2[kGO].y);
+                    const float Y = __fadd_rn(v2[kGV].x, v2[kGV].y);
+                    if (!GEOM) {
+                        vals[kGR] = __fadd_rn(v2[kGR].x, v2[kGR].y);
+                        vals[kGG] = __fadd_rn(v2[kGG].x, v2[kGG].y);
+                        vals[kGBl] = __fadd_rn(v2[kGBl].x, v2[kGBl].y);
+                        vals[kGO] = S;
+                    }
+                    vals[kGZ] = __fadd_rn(v2[kGZ].x, v2[kGZ].y);
+                    vals[kGC] = __fadd_rn(v2[kGC].x, v2[kGC].y);
+                    vals[kGV] = Y;
+                    vals[kGU] = __fmul_rn(dx, S);
+                    vals[kGA] = __fmul_rn(dx, vals[kGU]);
+                    vals[kGB] = __fmul_rn(dx, Y);
+                } else {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     if (pos >= last[p]) continue;
-                    const PairEval pe = eval_pair(px, (float)c.j[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y, q1.z);
+                    const PairEval pe = eval_pair(px, py[p], p0.x, p0.y, p0.z, p0.w, q1.x, q1.y, q1.z);
                     if (COUNT) ++n_proc;
                     if (!pe.pass) continue;
                     contrib = true;
@@ -480,6 +617,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                         vals[kGU] = __fadd_rn(vals[kGU], gx);
                         vals[kGV] = __fadd_rn(vals[kGV], gy);
                     }
+                }
                 }
                 if (DET) {
                     float sum;

@@ -218,6 +218,21 @@ __device__ __forceinline__ PairEval eval_pair(float px, float py, float u, float
     return e;
 }
 
+// The same evaluation for two pixels of one column (rows py.x and py.y) in packed
+// FP32 (Blackwell's paired FP32 instructions): every lane of __ffma2_rn /
+// __fmul2_rn / __fadd2_rn rounds as the scalar intrinsic does, so each lane equals
+// eval_pair bit for bit (a - b is formed as a + (-b), which rounds identically).
+// dx is the pixels' common column offset __fsub_rn(px, u).
+__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ void eval_pair2(float dx, float2 py, float v, float a, float b, float c, float lo2,
+                                           float2 &dy, float2 &p, float2 &l) {
+    dy = __fadd2_rn(py, bcast2(-v));
+    const float2 t = __ffma2_rn(bcast2(a), bcast2(dx), __fmul2_rn(bcast2(b), dy));
+    p = __ffma2_rn(bcast2(dx), t, __fmul2_rn(__fmul2_rn(bcast2(c), dy), dy));
+    l = __fadd2_rn(p, bcast2(lo2));
+}
+
 // 2^x with the hardware approximation (relative error below 2^-22); every
 // exponent reaching it lies in [log2(1/255), log2(0.99)] (to within the rounding
 // of the pass threshold), far from denormals.
