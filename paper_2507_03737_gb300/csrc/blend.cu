@@ -197,12 +197,12 @@ __global__ void __launch_bounds__(TW *TH / P) blend_fwd_kernel(const BlendArgs a
                 if constexpr (P % 2 == 0) {
                     // the quadratic form of two pixels of the column at once (packed FP32,
                     // each lane rounding as eval_pair does); the rest per pixel
-                    const float dx = __fsub_rn(px, p0.x);
+                    const ColTerms ct = col_terms(px, p0.x, p0.z, p0.w);
 #pragma unroll
                     for (int h = 0; h < P / 2; ++h) {
                         if (done[2 * h] && done[2 * h + 1]) continue;
                         float2 dy, pp, ll;
-                        eval_pair2(dx, make_float2(py[2 * h], py[2 * h + 1]), p0.y, p0.z, p0.w, p1.x, p1.y, dy, pp, ll);
+                        eval_pair2(ct, make_float2(py[2 * h], py[2 * h + 1]), p0.y, p1.x, p1.y, dy, pp, ll);
 #pragma unroll
                         for (int e2 = 0; e2 < 2; ++e2) {
                             const int p = 2 * h + e2;
@@ -341,12 +341,12 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                     if constexpr (P % 2 == 0) {
                         // the forward's evaluation (packed quadratic form, per-pixel decisions),
                         // T and the last index only
-                        const float dx = __fsub_rn(px, p0.x);
+                        const ColTerms ct = col_terms(px, p0.x, p0.z, p0.w);
 #pragma unroll
                         for (int h = 0; h < P / 2; ++h) {
                             if (done[2 * h] && done[2 * h + 1]) continue;
                             float2 dy, pp, ll;
-                            eval_pair2(dx, make_float2(py[2 * h], py[2 * h + 1]), p0.y, p0.z, p0.w, q1.x, q1.y, dy, pp, ll);
+                            eval_pair2(ct, make_float2(py[2 * h], py[2 * h + 1]), p0.y, q1.x, q1.y, dy, pp, ll);
 #pragma unroll
                             for (int e2 = 0; e2 < 2; ++e2) {
                                 const int p = 2 * h + e2;
@@ -511,7 +511,8 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                     // (S = sum g, Y = sum g dy), so per pair only S, Y and sum g dy^2 are
                     // accumulated.
                     const float4 col = s_col[k];
-                    const float dx = __fsub_rn(px, p0.x);
+                    const ColTerms ct = col_terms(px, p0.x, p0.z, p0.w);
+                    const float dx = ct.dx;
                     float2 v2[kGrad2d];
 #pragma unroll
                     for (int q = 0; q < kGrad2d; ++q) v2[q] = make_float2(0.f, 0.f);
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(TW *TH / P) blend_bwd_kernel(const BlendArgs a
                         const int r0 = 2 * h, r1 = 2 * h + 1;
                         if (pos >= last[r0] && pos >= last[r1]) continue;
                         float2 dy, pp, ll;
-                        eval_pair2(dx, make_float2(py[r0], py[r1]), p0.y, p0.z, p0.w, q1.x, q1.y, dy, pp, ll);
+                        eval_pair2(ct, make_float2(py[r0], py[r1]), p0.y, q1.x, q1.y, dy, pp, ll);
                         const bool c0 = pos < last[r0] && pp.x >= q1.z, c1 = pos < last[r1] && pp.y >= q1.z;
                         if (COUNT) n_proc += (unsigned long long)(pos < last[r0]) + (unsigned long long)(pos < last[r1]);
                         if (!(c0 || c1)) continue;  // neither pixel passes the cutoff and skip

@@ -205,13 +205,28 @@ struct PairEval {
     bool clamped;  // alpha hit the 0.99 clamp
 };
 
+// The terms of p that depend on the column only: p = a dx^2 + b dx dy + c dy^2 is
+// evaluated as (a dx) dx + dy (b dx + c dy), so a thread whose pixels share a
+// column forms A0 = (a dx) dx and B0 = b dx once per Gaussian.
+struct ColTerms {
+    float dx, A0, B0;
+};
+
+__device__ __forceinline__ ColTerms col_terms(float px, float u, float a, float b) {
+    ColTerms t;
+    t.dx = __fsub_rn(px, u);
+    t.A0 = __fmul_rn(__fmul_rn(a, t.dx), t.dx);
+    t.B0 = __fmul_rn(b, t.dx);
+    return t;
+}
+
 __device__ __forceinline__ PairEval eval_pair(float px, float py, float u, float v, float a, float b, float c,
                                               float lo2, float thr) {
+    const ColTerms ct = col_terms(px, u, a, b);
     PairEval e;
-    e.dx = __fsub_rn(px, u);
+    e.dx = ct.dx;
     e.dy = __fsub_rn(py, v);
-    const float t = __fmaf_rn(a, e.dx, __fmul_rn(b, e.dy));
-    const float p = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(c, e.dy), e.dy));
+    const float p = __fmaf_rn(e.dy, __fmaf_rn(c, e.dy, ct.B0), ct.A0);
     e.l = __fadd_rn(p, lo2);
     e.pass = p >= thr;
     e.clamped = e.l >= kClampL;
@@ -220,16 +235,14 @@ __device__ __forceinline__ PairEval eval_pair(float px, float py, float u, float
 
 // The same evaluation for two pixels of one column (rows py.x and py.y) in packed
 // FP32 (Blackwell's paired FP32 instructions): every lane of __ffma2_rn /
-// __fmul2_rn / __fadd2_rn rounds as the scalar intrinsic does, so each lane equals
-// eval_pair bit for bit (a - b is formed as a + (-b), which rounds identically).
-// dx is the pixels' common column offset __fsub_rn(px, u).
+// __fadd2_rn rounds as the scalar intrinsic does, so each lane equals eval_pair
+// bit for bit (a - b is formed as a + (-b), which rounds identically).
 __device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
 
-__device__ __forceinline__ void eval_pair2(float dx, float2 py, float v, float a, float b, float c, float lo2,
-                                           float2 &dy, float2 &p, float2 &l) {
+__device__ __forceinline__ void eval_pair2(const ColTerms &ct, float2 py, float v, float c, float lo2, float2 &dy,
+                                           float2 &p, float2 &l) {
     dy = __fadd2_rn(py, bcast2(-v));
-    const float2 t = __ffma2_rn(bcast2(a), bcast2(dx), __fmul2_rn(bcast2(b), dy));
-    p = __ffma2_rn(bcast2(dx), t, __fmul2_rn(__fmul2_rn(bcast2(c), dy), dy));
+    p = __ffma2_rn(dy, __ffma2_rn(bcast2(c), dy, bcast2(ct.B0)), bcast2(ct.A0));
     l = __fadd2_rn(p, bcast2(lo2));
 }
 
