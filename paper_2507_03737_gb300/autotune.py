@@ -5,7 +5,8 @@ None of these choices changes forward results (the per-pixel 3-sigma test is
 explicit, so tiles are only a conservative cover); they change only the
 summation order of atomically accumulated gradients. The tuner times a
 forward + backward of the caller's own workload with CUDA events and keeps the
-fastest option set, by coordinate descent from the library defaults. Results
+fastest option set, by coordinate descent from the caller's base schedule (the
+library defaults unless one is given). Results
 are cached in a JSON file keyed by a workload signature.
 """
 from __future__ import annotations
@@ -25,7 +26,7 @@ SEARCH_SPACE = {
     "pixels_per_thread": [1, 2, 4],
     "bwd_pixels_per_thread": [1, 2, 4],
     "batch": [64, 128, 256, 512],
-    "blocks_per_sm": [0, 2, 4, 8, 16],
+    "blocks_per_sm": [0, 2, 4, 8, 12, 16],
 }
 FIELDS = ("tile_w", "tile_h", "pixels_per_thread", "bwd_pixels_per_thread", "batch", "blocks_per_sm")
 
