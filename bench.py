@@ -722,7 +722,7 @@ def run_native(args):
 # The other workloads and SLAM rows a default run reports beside the headline, each
 # in a process of its own (so its device memory is released), with few steps and a
 # time limit; (label, extra arguments, steps).
-EXTRAS = [("config2", ["--config", "2"], 10), ("config4", ["--config", "4"], 10),
+EXTRAS = [("config1", ["--config", "1"], 50), ("config2", ["--config", "2"], 10), ("config4", ["--config", "4"], 10),
           ("config5", ["--config", "5"], 5), ("align", ["--row", "align"], 20),
           ("pose", ["--row", "pose"], 5), ("mapping", ["--row", "mapping"], 5), ("covis", ["--row", "covis"], 20)]
 EXTRAS_BUDGET_S = 300.0
