@@ -1043,7 +1043,8 @@ def run_pose(args):
         roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "ms_per_launch": stages[dominant],
                 "flops_per_launch": flops[dominant], "pairs": cnt,
-                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz", "peak_of": peak_src}
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (nominal FMA rate)",
+                "peak_of": "nominal"}
     elif dominant is not None:
         roof = {"kernel": dominant, "bound": "unclassified", "ms_per_launch": stages[dominant]}
     cpu = None
