@@ -227,7 +227,10 @@ s3gs_status s3gs_mapping_loss(s3gs_ctx *ctx, const s3gs_camera *cams, int32_t n_
  * Its partial sums live in a fixed 8 KB static device array (64 per view, so
  * n_views <= S3GS_MAX_VIEWS); larger requests return S3GS_E_INVALID. The first
  * call on each device looks up that array's address (cudaGetSymbolAddress),
- * so make one call per device before any stream capture. All calls share the
+ * so make one call per device before any stream capture (a first call on a
+ * capturing stream returns S3GS_E_INVALID and leaves the capture as it was);
+ * the address is cached for the life of the process, so do not call this entry
+ * point on a device after cudaDeviceReset. All calls share the
  * array: calls that overlap on the GPU (e.g. on two concurrent streams) race
  * and give wrong results; each call rewrites every partial it reads, so
  * nothing needs clearing between calls. err (optional, err_len bytes) receives

@@ -14,7 +14,10 @@
 // library holds its 8 KB until the process exits. Host code must never pass
 // the array's name to a kernel (on the host it is only a stand-in for the
 // symbol); its device address is obtained once per device with
-// cudaGetSymbolAddress and cached.
+// cudaGetSymbolAddress and cached for the life of the process. A cached address is
+// valid only while the device's context lives: after cudaDeviceReset the module may
+// load at another address, so a caller that resets a device must not call this entry
+// point on it again.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -37,10 +40,20 @@ void put_error(char *buf, size_t len, const char *msg) {
     if (buf && len > 0) snprintf(buf, len, "%s", msg);
 }
 
-// Device address of g_loss_partials on the current device (set-up on first use).
-cudaError_t partials_address(int device, float **out) {
+// Device address of g_loss_partials on the current device (set-up on first use). The
+// set-up may load the module, which must not happen inside a stream capture: a first call
+// on a capturing stream is refused (*capturing = true) and leaves the capture untouched.
+cudaError_t partials_address(int device, cudaStream_t stream, float **out, bool *capturing) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
+    *capturing = false;
     if (!g_partials_ptr[device]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing(stream, &cs);
+        if (ce != cudaSuccess) return ce;
+        if (cs != cudaStreamCaptureStatusNone) {
+            *capturing = true;
+            return cudaSuccess;
+        }
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_loss_partials);
         if (e != cudaSuccess) return e;
@@ -104,7 +117,13 @@ extern "C" s3gs_status s3gs_mapping_loss_noalloc(const s3gs_camera *cams, int32_
         return S3GS_E_INVALID;
     }
     float *partials = nullptr;
-    if (e == cudaSuccess) e = partials_address(device, &partials);
+    bool capturing = false;
+    if (e == cudaSuccess) e = partials_address(device, static_cast<cudaStream_t>(stream), &partials, &capturing);
+    if (e == cudaSuccess && capturing) {
+        put_error(err, err_len, "mapping_loss_noalloc: the first call on a device sets up the scratch address and "
+                                "must not be made while its stream is being captured; call it once before capture");
+        return S3GS_E_INVALID;
+    }
     if (e == cudaSuccess) {
         LossArgs la;
         la.rgb = rgb; la.depth = depth; la.pointmap = pointmap;
