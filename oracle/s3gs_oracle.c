@@ -748,42 +748,75 @@ int or_render_bwd(int64_t n, int sh_degree, const double *means, const double *l
  * tiles of tw x th pixels that this rectangle touches, the record is listed in
  * those whose box of pixel centres (inside the view) meets its ellipse
  * q(d) = A dx^2 + 2 B dx dy + C dy^2 <= q_cover (when conic and q_cover are
- * given; else in all of them): the smallest q over the box is 0 if the centre
- * lies in the box, else the least of the four edges' clamped one-dimensional
- * minima (stationary points from the reciprocals 1/A and 1/C), evaluated in
- * FP32 in the order written below. It is emitted once per
- * listed tile, in row-major tile order, with key (global tile id << 32) |
- * bits(z) and value g. Global tile ids number the tiles of view 0 first,
- * row-major, then view 1, and so on. Keys are sorted stably, so equal keys
- * keep ascending g. */
-static float or_edge_min_q(float a, float b, float c, float ic, float x, float lo, float hi) {
-    /* min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0, ic = 1 / c) */
-    float y = -(b * x) * ic;
-    y = fminf(fmaxf(y, lo), hi);
-    float t1 = a * (x * x);
-    float t2 = (2.0f * b) * (x * y);
-    float t3 = c * (y * y);
-    return (t1 + t2) + t3;
+ * given; else in all of them), taken one tile row at a time: the part of the
+ * ellipse inside the row's band of pixel-centre rows is convex, its x-extent
+ * runs from the left boundary dx = (-B dy - sqrt(A qc - det dy^2)) / A at
+ * dy_L = B sqrt(qc / (C det)) clamped to the band to the right boundary
+ * (+sqrt) at -dy_L clamped to the band (det = A C - B^2; nothing beyond
+ * |dy| > sqrt(A qc / det)), widened by 1e-5 of its terms, 7e-4 sqrt(qc / A) and
+ * 1e-3 px, and a tile is listed iff its columns of pixel centres meet that
+ * interval. All of it in FP32 in the order written below (the library takes the
+ * same decisions with the same operations, so the lists can be compared bit for
+ * bit; whether the cover misses a contributing pixel is checked separately, from
+ * the FP64 projection). It is emitted once per listed tile, in row-major tile
+ * order, with key (global tile id << 32) | bits(z) and value g. Global tile ids
+ * number the tiles of view 0 first, row-major, then view 1, and so on. Keys are
+ * sorted stably, so equal keys keep ascending g. */
+typedef struct {
+    float u, v, B, iA, Aqc, det, ym, yL, mq;
+} or_cover;
+
+static or_cover or_cover_of(float u, float v, float A, float B, float C, float qc) {
+    or_cover e;
+    e.u = u;
+    e.v = v;
+    e.B = B;
+    e.iA = 1.0f / A;
+    e.Aqc = A * qc;
+    e.det = fmaf(A, C, -(B * B));
+    if (!(qc >= 0.0f)) {
+        e.ym = -1.0f;
+        e.yL = 0.0f;
+        e.mq = 0.0f;
+        return e;
+    }
+    float g = e.det > 0.0f ? qc / e.det : 0.0f;
+    e.ym = e.det > 0.0f ? fmaf(sqrtf(A * g), 1.00001f, 1e-3f) : 3.0e38f;
+    e.yL = e.det > 0.0f ? B * sqrtf(g / C) : 0.0f;
+    e.mq = fmaf(7e-4f, sqrtf(qc * e.iA), 1e-3f);
+    return e;
 }
 
-static int or_tile_hit(float u, float v, float A, float B, float C, float qc, int px0, int px1, int py0, int py1) {
-    float dx0 = (float)px0 - u, dx1 = (float)px1 - u, dy0 = (float)py0 - v, dy1 = (float)py1 - v;
-    float iA = 1.0f / A, iC = 1.0f / C;
-    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return qc >= 0.0f;
-    float m = or_edge_min_q(A, B, C, iC, dx0, dy0, dy1);
-    m = fminf(m, or_edge_min_q(A, B, C, iC, dx1, dy0, dy1));
-    m = fminf(m, or_edge_min_q(C, B, A, iA, dy0, dx0, dx1));
-    m = fminf(m, or_edge_min_q(C, B, A, iA, dy1, dx0, dx1));
-    return m <= qc;
+/* listed tile columns [*c0, *c1] of the tile row with pixel-centre rows [py0, py1] */
+static void or_row_span(const or_cover *e, int py0, int py1, int tx0, int tx1, float inv_tw, int *c0, int *c1) {
+    float lo = fmaxf((float)py0 - e->v, -e->ym);
+    float hi = fminf((float)py1 - e->v, e->ym);
+    if (!(lo <= hi)) { *c0 = 1; *c1 = 0; return; }
+    if (!(e->det > 0.0f)) { *c0 = tx0; *c1 = tx1; return; }
+    float yl = fminf(fmaxf(e->yL, lo), hi), yr = fminf(fmaxf(-e->yL, lo), hi);
+    float sl = sqrtf(fmaxf(fmaf(-e->det, yl * yl, e->Aqc), 0.0f));
+    float sr = sqrtf(fmaxf(fmaf(-e->det, yr * yr, e->Aqc), 0.0f));
+    float byl = e->B * yl, byr = e->B * yr;
+    float xl = (-byl - sl) * e->iA;
+    float xr = (-byr + sr) * e->iA;
+    float ml = fmaf(1e-5f, (fabsf(byl) + sl) * e->iA, e->mq);
+    float mr = fmaf(1e-5f, (fabsf(byr) + sr) * e->iA, e->mq);
+    float a = (e->u + xl) - ml, b = (e->u + xr) + mr;
+    float f0 = fminf(fmaxf(ceilf((a + 1.0f) * inv_tw) - 1.0f, (float)tx0), (float)(tx1 + 1));
+    float f1 = fmaxf(fminf(floorf(b * inv_tw), (float)tx1), (float)(tx0 - 1));
+    *c0 = (int)f0;
+    *c1 = (int)f1;
 }
 
-static int or_listed(const float *conic, const float *qcover, int64_t r, float u, float v, int tx, int ty, int tw,
-                     int th, int W, int H) {
-    if (!conic || !qcover) return 1;
-    int px0 = tx * tw, px1 = px0 + tw - 1 < W - 1 ? px0 + tw - 1 : W - 1;
+/* listed columns of one tile row of record r (all of the rectangle without a conic) */
+static void or_listed_span(const float *conic, const float *qcover, int64_t r, float u, float v, int ty, int tx0,
+                           int tx1, int tw, int th, int H, int *c0, int *c1) {
+    if (!conic || !qcover) { *c0 = tx0; *c1 = tx1; return; }
+    or_cover e = or_cover_of(u, v, conic[3 * r], conic[3 * r + 1], conic[3 * r + 2], qcover[r]);
     int py0 = ty * th, py1 = py0 + th - 1 < H - 1 ? py0 + th - 1 : H - 1;
-    return or_tile_hit(u, v, conic[3 * r], conic[3 * r + 1], conic[3 * r + 2], qcover[r], px0, px1, py0, py1);
+    or_row_span(&e, py0, py1, tx0, tx1, 1.0f / (float)tw, c0, c1);
 }
+
 typedef struct {
     uint64_t key;
     int64_t order;
@@ -832,8 +865,11 @@ int64_t or_bin_referee(int64_t n, int n_views, const int32_t *view_wh, int tw, i
             int64_t r = (int64_t)vv * n + g;
             int a, b, c, d;
             if (!or_rect(u[r], v[r], rx[r], ry[r], W, H, tw, th, &a, &b, &c, &d)) continue;
-            for (int ty = b; ty <= d; ++ty)
-                for (int tx = a; tx <= c; ++tx) K += or_listed(conic, qcover, r, u[r], v[r], tx, ty, tw, th, W, H);
+            for (int ty = b; ty <= d; ++ty) {
+                int c0, c1;
+                or_listed_span(conic, qcover, r, u[r], v[r], ty, a, c, tw, th, H, &c0, &c1);
+                if (c1 >= c0) K += c1 - c0 + 1;
+            }
         }
     }
     if (!out_keys) { free(tile_base); return K; }
@@ -849,15 +885,17 @@ int64_t or_bin_referee(int64_t n, int n_views, const int32_t *view_wh, int tw, i
             if (!or_rect(u[r], v[r], rx[r], ry[r], W, H, tw, th, &a, &b, &c, &d)) continue;
             uint32_t zb;
             memcpy(&zb, &z[r], 4);
-            for (int ty = b; ty <= d; ++ty)
-                for (int tx = a; tx <= c; ++tx) {
-                    if (!or_listed(conic, qcover, r, u[r], v[r], tx, ty, tw, th, W, H)) continue;
+            for (int ty = b; ty <= d; ++ty) {
+                int c0, c1;
+                or_listed_span(conic, qcover, r, u[r], v[r], ty, a, c, tw, th, H, &c0, &c1);
+                for (int tx = c0; tx <= c1; ++tx) {
                     uint64_t tile = (uint64_t)(tile_base[vv] + (int64_t)ty * tiles_x + tx);
                     kv[e].key = (tile << 32) | zb;
                     kv[e].order = e;
                     kv[e].value = (uint32_t)g;
                     ++e;
                 }
+            }
         }
     }
     qsort(kv, (size_t)K, sizeof(or_kv), or_kv_cmp);

@@ -114,37 +114,38 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const ScanArgs a) {
     }
 }
 
-// One warp expands the (record, tile) pairs of its 32 records: an inclusive
-// warp scan of the records' tile counts numbers the pairs, and each round every
-// lane takes one pair (found by a 5-step search of the scan), so all lanes stay
-// busy whatever the mix of visible, culled, small and large records. Four rounds
-// of cursor atomics are issued before their results are consumed.
+// One warp expands the (record, tile) pairs of its 32 records in the two levels
+// of the projection's count: level 1 numbers the tile rows of the records'
+// bounding rectangles (a warp scan) and every lane computes one row's span of
+// covered tile columns with the same row_span the count used; level 2 numbers
+// the round's covered tiles and every lane emits one key per sub-round. All lanes
+// stay busy whatever the mix of visible, culled, small and large records, and
+// only covered tiles cost a cursor atomic. Four sub-rounds of cursor atomics
+// are issued before their results are consumed.
 __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __grid_constant__ ViewBatch vb) {
-    __shared__ unsigned s_incl[8][32], s_excl[8][32], s_origin[8][32], s_ntx[8][32], s_tx[8][32];
+    __shared__ unsigned s_incl[8][32], s_excl[8][32], s_t0[8][32], s_ntx[8][32], s_orig[8][32];
     __shared__ unsigned long long s_key[8][32];
     __shared__ CoverEllipse s_ell[8][32];  // cover ellipse of the source record
-    __shared__ unsigned s_t0[8][32];  // tx0 | ty0 << 16
-    __shared__ unsigned s_view[8][32];
     if (a.ctr->overflow) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // blockIdx.y is the view, so no record index needs dividing
     const int v = (int)blockIdx.y;
+    const ViewInfo &vi = vb.v[v];
     const long long gl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long r = (long long)v * a.n + gl;
-    unsigned cnt = 0, origin = 0, ntx = 1, tiles_x = 0, t0 = 0, view = 0;
+    unsigned nrows = 0, ntx = 1, t0 = 0, orig = 0;
     unsigned long long key = 0;
     CoverEllipse ell;
-    ell.u = ell.v = ell.A = ell.B = ell.C = ell.iA = ell.iC = ell.qc = 0.f;
+    ell.u = ell.v = ell.B = ell.iA = ell.Aqc = ell.det = ell.yL = ell.mq = 0.f;
+    ell.ym = -1.0f;
     if (gl < a.n) {
         const int2 ext = a.ext[r];
         if (ext.x > 0) {
             const unsigned g = (unsigned)gl;
-            const ViewInfo &vi = vb.v[v];
             const float4 ra = a.rec[r].a;
             const float4 rb = a.rec[r].b;
             const float z = rb.z;
             ell = cover_ellipse(ra.x, ra.y, ra.z, ra.w, rb.x, a.rec[r].c.w);
-            view = (unsigned)v;
             const float x0 = ceilf(__fsub_rn(ra.x, (float)ext.x)), x1 = floorf(__fadd_rn(ra.x, (float)ext.x));
             const float y0 = ceilf(__fsub_rn(ra.y, (float)ext.y)), y1 = floorf(__fadd_rn(ra.y, (float)ext.y));
             const int tx0 = tile_of(x0 > 0.f ? (int)x0 : 0, vb.tile_w);
@@ -152,62 +153,67 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
             const int ty0 = tile_of(y0 > 0.f ? (int)y0 : 0, vb.tile_h);
             const int ty1 = tile_of(y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1, vb.tile_h);
             ntx = (unsigned)(tx1 - tx0 + 1);
-            cnt = ntx * (unsigned)(ty1 - ty0 + 1);
+            nrows = (unsigned)(ty1 - ty0 + 1);
             t0 = (unsigned)tx0 | ((unsigned)ty0 << 16);
-            origin = (unsigned)(vi.tile_base + ty0 * vi.tiles_x + tx0) * kDepthBins + (unsigned)depth_bin(z);
-            tiles_x = (unsigned)vi.tiles_x * kDepthBins;
+            orig = (unsigned)(vi.tile_base + ty0 * vi.tiles_x) * kDepthBins + (unsigned)depth_bin(z);
             key = ((unsigned long long)__float_as_uint(z) << 32) | g;
         }
     }
-    unsigned incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
+    const unsigned incl = warp_incl_scan(nrows);
     const unsigned wtotal = __shfl_sync(0xffffffffu, incl, 31);
     if (wtotal == 0) return;
     s_incl[warp][lane] = incl;
-    s_excl[warp][lane] = incl - cnt;
-    s_origin[warp][lane] = origin;
+    s_excl[warp][lane] = incl - nrows;
+    s_t0[warp][lane] = t0;
     s_ntx[warp][lane] = ntx;
-    s_tx[warp][lane] = tiles_x;
+    s_orig[warp][lane] = orig;
     s_key[warp][lane] = key;
     s_ell[warp][lane] = ell;
-    s_t0[warp][lane] = t0;
-    s_view[warp][lane] = view;
     __syncwarp();
-    for (unsigned base = 0; base < wtotal; base += 4 * 32) {
-        unsigned pos[4];
-        unsigned long long kk[4];
+    const float inv_tw = __frcp_rn((float)vb.tile_w);  // exact: the tile width is a power of two
+    const unsigned row_stride = (unsigned)vi.tiles_x * kDepthBins;
+    for (unsigned base = 0; base < wtotal; base += 32) {
+        const unsigned j = base + lane;
+        int c0 = 0;
+        unsigned len = 0, rowbase = 0;
+        unsigned long long rkey = 0;
+        if (j < wtotal) {
+            unsigned src = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const unsigned j = base + u * 32 + lane;
-            pos[u] = 0xffffffffu;
-            if (j < wtotal) {
-                unsigned src = 0;
-#pragma unroll
-                for (unsigned b = 16; b > 0; b >>= 1)
-                    if (s_incl[warp][src + b - 1] <= j) src += b;
-                const unsigned local = j - s_excl[warp][src];
-                const unsigned nx = s_ntx[warp][src];
-                unsigned colm;
-                const unsigned row = div_small(local, nx, colm);
-                const unsigned tt = s_t0[warp][src];
-                const int tx = (int)(tt & 0xffffu) + (int)colm, ty = (int)(tt >> 16) + (int)row;
-                const ViewInfo &vi = vb.v[s_view[warp][src]];
-                const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
-                const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
-                if (tile_hit(s_ell[warp][src], px0, px1, py0, py1)) {
-                    const unsigned bucket = s_origin[warp][src] + row * s_tx[warp][src] + colm * kDepthBins;
-                    pos[u] = atomicAdd(a.cursor + bucket, 1u);
-                    kk[u] = s_key[warp][src];
-                }
-            }
+            for (unsigned b = 16; b > 0; b >>= 1)
+                if (s_incl[warp][src + b - 1] <= j) src += b;
+            const unsigned row = j - s_excl[warp][src];
+            const unsigned tt = s_t0[warp][src];
+            const int ty = (int)(tt >> 16) + (int)row;
+            const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
+            const int cx0 = (int)(tt & 0xffffu);
+            const int2 span = row_span(s_ell[warp][src], py0, py1, cx0, cx0 + (int)s_ntx[warp][src] - 1, inv_tw);
+            c0 = span.x;
+            len = span.y >= span.x ? (unsigned)(span.y - span.x + 1) : 0u;
+            rowbase = s_orig[warp][src] + row * row_stride;
+            rkey = s_key[warp][src];
         }
+        const unsigned incl2 = warp_incl_scan(len);
+        const unsigned tot2 = __shfl_sync(0xffffffffu, incl2, 31);
+        const unsigned excl2 = incl2 - len;
+        for (unsigned b2 = 0; b2 < tot2; b2 += 4 * 32) {
+            unsigned pos[4];
+            unsigned long long kk[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (pos[u] < a.key_capacity) a.keys[pos[u]] = kk[u];
+            for (int u = 0; u < 4; ++u) {
+                const unsigned j2 = b2 + u * 32 + lane;
+                const int src2 = warp_find(incl2, j2);
+                const int h0 = __shfl_sync(0xffffffffu, c0, src2);
+                const unsigned he = __shfl_sync(0xffffffffu, excl2, src2);
+                const unsigned hb = __shfl_sync(0xffffffffu, rowbase, src2);
+                kk[u] = __shfl_sync(0xffffffffu, rkey, src2);
+                pos[u] = 0xffffffffu;
+                if (j2 < tot2) pos[u] = atomicAdd(a.cursor + hb + (unsigned)(h0 + (int)(j2 - he)) * kDepthBins, 1u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (pos[u] < a.key_capacity) a.keys[pos[u]] = kk[u];
+        }
     }
 }
 

@@ -172,52 +172,51 @@ __device__ __forceinline__ float view_coord(const float *r, const float m[3], fl
 }
 
 // Counts the (tile, depth bin) buckets of the 32 records a warp has just made
-// for one view: an inclusive warp scan numbers the records' candidate tiles
-// (their bounding rectangles), and in each round every lane takes one
-// candidate, fetches its record's cover ellipse with shuffles, tests it and
-// counts it. All lanes stay busy whatever the mix of record sizes.
+// for one view, in two levels. Level 1: a warp scan numbers the tile rows of the
+// records' bounding rectangles; in each round every lane takes one (record, row),
+// fetches the record's cover ellipse with shuffles and computes the row's span of
+// covered tile columns (row_span). Level 2: a second scan numbers the round's
+// covered tiles, and in each sub-round every lane counts one. All lanes stay busy
+// whatever the mix of record sizes, and only covered tiles cost a count.
 __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const ViewBatch &vb, const ViewInfo &vi,
                                                  bool has, const CoverEllipse &ell, int tx0, int ty0, int ntx, int nty,
                                                  int bin) {
     const int lane = threadIdx.x & 31;
-    const unsigned cnt = has ? (unsigned)(ntx * nty) : 0u;
-    unsigned incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
+    const unsigned nrows = has ? (unsigned)nty : 0u;
+    const unsigned incl = warp_incl_scan(nrows);
     const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-    const unsigned excl = incl - cnt;
+    const unsigned excl = incl - nrows;
     const unsigned t0 = (unsigned)tx0 | ((unsigned)ty0 << 16);
+    const float inv_tw = __frcp_rn((float)vb.tile_w);  // exact: the tile width is a power of two
     for (unsigned base = 0; base < total; base += 32) {
         const unsigned j = base + lane;
-        int src = 0;
-#pragma unroll
-        for (int b = 16; b > 0; b >>= 1)
-            if (__shfl_sync(0xffffffffu, incl, src + b - 1) <= j) src += b;
-        src = src > 31 ? 31 : src;
-        CoverEllipse e;
-        e.u = __shfl_sync(0xffffffffu, ell.u, src);
-        e.v = __shfl_sync(0xffffffffu, ell.v, src);
-        e.A = __shfl_sync(0xffffffffu, ell.A, src);
-        e.B = __shfl_sync(0xffffffffu, ell.B, src);
-        e.C = __shfl_sync(0xffffffffu, ell.C, src);
-        e.iA = __shfl_sync(0xffffffffu, ell.iA, src);
-        e.iC = __shfl_sync(0xffffffffu, ell.iC, src);
-        e.qc = __shfl_sync(0xffffffffu, ell.qc, src);
+        const int src = warp_find(incl, j);
+        const CoverEllipse e = shfl_ellipse(ell, src);
         const unsigned s_excl = __shfl_sync(0xffffffffu, excl, src);
         const unsigned s_t0 = __shfl_sync(0xffffffffu, t0, src);
         const int s_ntx = __shfl_sync(0xffffffffu, ntx, src);
         const int s_bin = __shfl_sync(0xffffffffu, bin, src);
+        int c0 = 0;
+        unsigned len = 0, rowbase = 0;
         if (j < total) {
-            unsigned col;
-            const unsigned row = div_small(j - s_excl, (unsigned)s_ntx, col);
-            const int tx = (int)(s_t0 & 0xffffu) + (int)col, ty = (int)(s_t0 >> 16) + (int)row;
-            const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
+            const int ty = (int)(s_t0 >> 16) + (int)(j - s_excl);
             const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
-            if (tile_hit(e, px0, px1, py0, py1))
-                atomicAdd(a.tile_count + (size_t)(vi.tile_base + ty * vi.tiles_x + tx) * kDepthBins + s_bin, 1u);
+            const int cx0 = (int)(s_t0 & 0xffffu);
+            const int2 span = row_span(e, py0, py1, cx0, cx0 + s_ntx - 1, inv_tw);
+            c0 = span.x;
+            len = span.y >= span.x ? (unsigned)(span.y - span.x + 1) : 0u;
+            rowbase = (unsigned)(vi.tile_base + ty * vi.tiles_x) * kDepthBins + (unsigned)s_bin;
+        }
+        const unsigned incl2 = warp_incl_scan(len);
+        const unsigned tot2 = __shfl_sync(0xffffffffu, incl2, 31);
+        const unsigned excl2 = incl2 - len;
+        for (unsigned b2 = 0; b2 < tot2; b2 += 32) {
+            const unsigned j2 = b2 + lane;
+            const int src2 = warp_find(incl2, j2);
+            const int h0 = __shfl_sync(0xffffffffu, c0, src2);
+            const unsigned he = __shfl_sync(0xffffffffu, excl2, src2);
+            const unsigned hb = __shfl_sync(0xffffffffu, rowbase, src2);
+            if (j2 < tot2) atomicAdd(a.tile_count + hb + (size_t)(h0 + (int)(j2 - he)) * kDepthBins, 1u);
         }
     }
 }
@@ -249,7 +248,8 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
         int2 ext = make_int2(0, 0);
         bool has = false;
         CoverEllipse ell;
-        ell.u = ell.v = ell.A = ell.B = ell.C = ell.iA = ell.iC = ell.qc = 0.f;
+        ell.u = ell.v = ell.B = ell.iA = ell.Aqc = ell.det = ell.yL = ell.mq = 0.f;
+        ell.ym = -1.0f;
         int ctx0 = 0, cty0 = 0, cntx = 0, cnty = 0, cbin = 0;
         float T[12];
         load_pose(vi, a.Tdev, v, T);

@@ -59,11 +59,11 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
 #pragma unroll
     for (int q = 0; q < kGrad2d; ++q) acc[q] = 0.f;
     const CoverEllipse ell = cover_ellipse(ra.x, ra.y, ra.z, ra.w, a.rec[r].b.x, a.rec[r].c.w);
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const int px0 = tx * vb.tile_w, px1 = min(px0 + vb.tile_w - 1, vi.w - 1);
-            const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
-            if (!tile_hit(ell, px0, px1, py0, py1)) continue;  // not listed there
+    const float inv_tw = __frcp_rn((float)vb.tile_w);
+    for (int ty = ty0; ty <= ty1; ++ty) {
+        const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
+        const int2 span = row_span(ell, py0, py1, tx0, tx1, inv_tw);  // the tiles the record is listed in
+        for (int tx = span.x; tx <= span.y; ++tx) {
             int t = vi.tile_base + ty * vi.tiles_x + tx;
             unsigned lo = a.tile_start[t * kDepthBins], hi = a.tile_start[(t + 1) * kDepthBins];
             while (lo < hi) {
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
 #pragma unroll
             for (int q = 0; q < kGrad2d; ++q) acc[q] += src[q];
         }
+    }
     float *dst = a.grad2d + r * kGrad2d;
 #pragma unroll
     for (int q = 0; q < kGrad2d; ++q) dst[q] = acc[q];

@@ -88,7 +88,7 @@ struct ViewBatch {
 struct __align__(16) Record {
     float4 a;  // u, v, A, B  (conic = [[A, B], [B, C]])
     float4 b;  // C, opacity, z, log2(opacity)
-    float4 c;  // r, g, b, q_cover (the tile-cover bound on q, see tile_hit)
+    float4 c;  // r, g, b, q_cover (the tile-cover bound on q, see row_span)
 };
 
 // Tile cover. A record is listed in a tile only if its ellipse q(d) <= q_cover,
@@ -96,44 +96,110 @@ struct __align__(16) Record {
 // the tile's pixels inside the image. q_cover is the largest q at which the
 // blend can accept a pair -- min(9, 2 ln 2 (log2 opacity - log2(1/255))), the
 // 3-sigma cutoff or the 1/255 skip -- widened for FP32 rounding of the conic
-// (relative 2e-5 plus 8e-7 times its condition number). The smallest q over
-// the box lies on its border unless the centre is inside; on each edge it is a
-// clamped one-dimensional minimum, whose stationary point uses the reciprocals
-// 1/A and 1/C (each a correctly rounded division, taken once per record). Every
-// operation is an explicit round-to-nearest intrinsic, so the projection's
-// counts, the emission and the deterministic reduce take identical decisions
-// (and the integer referee can repeat them in plain C).
-__device__ __forceinline__ float edge_min_q(float a, float b, float c, float ic, float x, float lo, float hi) {
-    // min over y in [lo, hi] of a x^2 + 2 b x y + c y^2 (c > 0, ic = 1 / c)
-    float y = __fmul_rn(-__fmul_rn(b, x), ic);
-    y = fminf(fmaxf(y, lo), hi);
-    const float t1 = __fmul_rn(a, __fmul_rn(x, x));
-    const float t2 = __fmul_rn(__fmul_rn(2.0f, b), __fmul_rn(x, y));
-    const float t3 = __fmul_rn(c, __fmul_rn(y, y));
-    return __fadd_rn(__fadd_rn(t1, t2), t3);
-}
-
+// (relative 2e-5 plus 8e-7 times its condition number).
+//
+// The cover is taken one tile row at a time. The part of the ellipse inside the
+// row's band of pixel-centre rows dy in [lo, hi] is convex, so its x-extent is an
+// interval, and a tile of the row meets the ellipse iff its columns of pixel
+// centres meet that interval. For fixed dy the ellipse spans
+// dx = (-B dy -/+ sqrt(A q_cover - det dy^2)) / A (det = A C - B^2); its leftmost
+// point lies at dy_L = B sqrt(q_cover / (C det)) and its rightmost at -dy_L, so
+// the band's interval runs from the left boundary at dy_L clamped to the band to
+// the right boundary at -dy_L clamped to the band, and the band is empty beyond
+// |dy| > sqrt(A q_cover / det). The interval is widened by 1e-5 of its terms,
+// by 7e-4 sqrt(q_cover / A) (the square root's sensitivity where the span
+// narrows to a point) and by 1e-3 px, so that it contains every column at which
+// the FP32 blend can pass; a tile listed needlessly only costs evaluations. The
+// tile range is rounded outwards and clamped to the record's bounding
+// rectangle. Every operation is an explicit round-to-nearest intrinsic (or an
+// exact min/max/ceil/floor), so the projection's counts, the emission and the
+// deterministic reduce list identical tiles, and the integer referee can repeat
+// the arithmetic in plain C.
 struct CoverEllipse {
-    float u, v, A, B, C, iA, iC, qc;
+    float u, v, B, iA;
+    float Aqc, det, ym, yL;  // A q_cover, A C - B^2, the band limit sqrt(A q_cover / det), dy_L
+    float mq;                // absolute widening (px): 7e-4 sqrt(q_cover / A) + 1e-3
 };
 
 __device__ __forceinline__ CoverEllipse cover_ellipse(float u, float v, float A, float B, float C, float qc) {
     CoverEllipse e;
-    e.u = u; e.v = v; e.A = A; e.B = B; e.C = C; e.qc = qc;
+    e.u = u;
+    e.v = v;
+    e.B = B;
     e.iA = __fdiv_rn(1.0f, A);
-    e.iC = __fdiv_rn(1.0f, C);
+    e.Aqc = __fmul_rn(A, qc);
+    e.det = __fmaf_rn(A, C, -__fmul_rn(B, B));
+    if (!(qc >= 0.f)) {
+        e.ym = -1.0f;  // q_cover < 0: the record reaches no pixel
+        e.yL = 0.f;
+        e.mq = 0.f;
+        return e;
+    }
+    const float g = e.det > 0.f ? __fdiv_rn(qc, e.det) : 0.f;
+    e.ym = e.det > 0.f ? __fmaf_rn(__fsqrt_rn(__fmul_rn(A, g)), 1.00001f, 1e-3f) : 3.0e38f;
+    e.yL = e.det > 0.f ? __fmul_rn(B, __fsqrt_rn(__fdiv_rn(g, C))) : 0.f;
+    e.mq = __fmaf_rn(7e-4f, __fsqrt_rn(__fmul_rn(qc, e.iA)), 1e-3f);
     return e;
 }
 
-__device__ __forceinline__ bool tile_hit(const CoverEllipse &e, int px0, int px1, int py0, int py1) {
-    const float dx0 = __fsub_rn((float)px0, e.u), dx1 = __fsub_rn((float)px1, e.u);
-    const float dy0 = __fsub_rn((float)py0, e.v), dy1 = __fsub_rn((float)py1, e.v);
-    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return e.qc >= 0.f;
-    float m = edge_min_q(e.A, e.B, e.C, e.iC, dx0, dy0, dy1);
-    m = fminf(m, edge_min_q(e.A, e.B, e.C, e.iC, dx1, dy0, dy1));
-    m = fminf(m, edge_min_q(e.C, e.B, e.A, e.iA, dy0, dx0, dx1));
-    m = fminf(m, edge_min_q(e.C, e.B, e.A, e.iA, dy1, dx0, dx1));
-    return m <= e.qc;
+// Tile columns [c.x, c.y] (empty when c.y < c.x) of the tile row whose pixel-centre
+// rows are [py0, py1] that meet the record's ellipse, within the rectangle's columns
+// [tx0, tx1]; inv_tw = 1 / tile width (a power of two, so the product is exact).
+__device__ __forceinline__ int2 row_span(const CoverEllipse &e, int py0, int py1, int tx0, int tx1, float inv_tw) {
+    const float lo = fmaxf(__fsub_rn((float)py0, e.v), -e.ym);
+    const float hi = fminf(__fsub_rn((float)py1, e.v), e.ym);
+    if (!(lo <= hi)) return make_int2(1, 0);
+    if (!(e.det > 0.f)) return make_int2(tx0, tx1);  // degenerate conic: the whole rectangle row
+    const float yl = fminf(fmaxf(e.yL, lo), hi), yr = fminf(fmaxf(-e.yL, lo), hi);
+    const float sl = __fsqrt_rn(fmaxf(__fmaf_rn(-e.det, __fmul_rn(yl, yl), e.Aqc), 0.f));
+    const float sr = __fsqrt_rn(fmaxf(__fmaf_rn(-e.det, __fmul_rn(yr, yr), e.Aqc), 0.f));
+    const float byl = __fmul_rn(e.B, yl), byr = __fmul_rn(e.B, yr);
+    const float xl = __fmul_rn(__fsub_rn(-byl, sl), e.iA);
+    const float xr = __fmul_rn(__fadd_rn(-byr, sr), e.iA);
+    const float ml = __fmaf_rn(1e-5f, __fmul_rn(__fadd_rn(fabsf(byl), sl), e.iA), e.mq);
+    const float mr = __fmaf_rn(1e-5f, __fmul_rn(__fadd_rn(fabsf(byr), sr), e.iA), e.mq);
+    const float a = __fsub_rn(__fadd_rn(e.u, xl), ml), b = __fadd_rn(__fadd_rn(e.u, xr), mr);
+    // tile c holds centre columns [c tw, c tw + tw - 1]: it meets [a, b] iff
+    // c >= ceil((a + 1) / tw) - 1 and c <= floor(b / tw)
+    const float c0 = fminf(fmaxf(__fsub_rn(ceilf(__fmul_rn(__fadd_rn(a, 1.0f), inv_tw)), 1.0f), (float)tx0),
+                           (float)(tx1 + 1));
+    const float c1 = fmaxf(fminf(floorf(__fmul_rn(b, inv_tw)), (float)tx1), (float)(tx0 - 1));
+    return make_int2((int)c0, (int)c1);
+}
+
+// Warp helpers of the two-level cover enumeration: an inclusive scan of one
+// count per lane, and the lane whose interval [incl - count, incl) holds j (a
+// 5-step search over the scan; every lane must take part).
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int warp_find(unsigned incl, unsigned j) {
+    int src = 0;
+#pragma unroll
+    for (int b = 16; b > 0; b >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, src + b - 1) <= j) src += b;
+    return src > 31 ? 31 : src;
+}
+
+__device__ __forceinline__ CoverEllipse shfl_ellipse(const CoverEllipse &e, int src) {
+    CoverEllipse r;
+    r.u = __shfl_sync(0xffffffffu, e.u, src);
+    r.v = __shfl_sync(0xffffffffu, e.v, src);
+    r.B = __shfl_sync(0xffffffffu, e.B, src);
+    r.iA = __shfl_sync(0xffffffffu, e.iA, src);
+    r.Aqc = __shfl_sync(0xffffffffu, e.Aqc, src);
+    r.det = __shfl_sync(0xffffffffu, e.det, src);
+    r.ym = __shfl_sync(0xffffffffu, e.ym, src);
+    r.yL = __shfl_sync(0xffffffffu, e.yL, src);
+    r.mq = __shfl_sync(0xffffffffu, e.mq, src);
+    return r;
 }
 
 struct DevCounters {
