@@ -114,6 +114,12 @@ typedef struct {
     float near_z;            /* cull Gaussians with view-space z <= near_z (0 = 0.2) */
     float guard_slope;       /* guard cone G (0 = 1.5; negative = no cone) */
     float bg[3];             /* background colour composited with the final transmittance */
+    int32_t full_lists;      /* 0 (default): occlusion cut. Each tile's list ends after the first
+                                depth bin by which the Gaussians that cover the whole tile are
+                                certain, by a bound with FP32 margins, to have driven every pixel
+                                of the tile below the 1e-4 transmittance stop of Eq. 2; no pixel
+                                reaches a later bin, so outputs and gradients are unchanged.
+                                1: list every covered (tile, Gaussian) pair. */
 } s3gs_options;
 
 /* Fill *opt with the defaults (16x16 tiles, 2 / 4 pixels per forward / backward

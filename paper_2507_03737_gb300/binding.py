@@ -62,7 +62,7 @@ class Options(ctypes.Structure):
                 ("batch", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("deterministic", ctypes.c_int32), ("recompute", ctypes.c_int32),
                 ("auto_grow", ctypes.c_int32), ("near_z", ctypes.c_float), ("guard_slope", ctypes.c_float),
-                ("bg", ctypes.c_float * 3)]
+                ("bg", ctypes.c_float * 3), ("full_lists", ctypes.c_int32)]
 
 
 class AlignParams(ctypes.Structure):

@@ -70,6 +70,8 @@ struct s3gs_state {
     DevBuf<unsigned> vis_mask;
     DevBuf<float> grad2d;
     DevBuf<unsigned> tile_count, tile_start, cursor, order, scan_part;
+    DevBuf<unsigned> occl;        // per bucket optical depth lower bound (occlusion cut)
+    DevBuf<unsigned char> cut;    // per tile last listed depth bin
     DevBuf<unsigned long long> keys;       // tile-sorted duplicate list
     DevBuf<unsigned long long> keys_emit;  // emission order, read by the tile sort
     DevBuf<float> det_partial;
@@ -240,6 +242,8 @@ s3gs_status ensure_forward_buffers(s3gs_ctx *ctx, s3gs_state *st, long long n_re
     if ((r = grow(ctx, st->cursor, n_buckets + 1, s, "cursor")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->order, n_tiles + 1, s, "order")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->scan_part, (n_buckets + 4095) / 4096 + 2, s, "scan_part")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->occl, n_buckets + 1, s, "occlusion")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->cut, n_tiles + 16, s, "cut")) != S3GS_OK) return r;
     if (store) {
         if ((r = grow(ctx, st->T_final, n_pix, s, "T_final")) != S3GS_OK) return r;
         if ((r = grow(ctx, st->n_last, n_pix, s, "n_last")) != S3GS_OK) return r;
@@ -372,7 +376,7 @@ void s3gs_state_destroy(s3gs_state *st) {
     void *bufs[] = {st->rec.p,       st->ext.p,       st->vis_mask.p,  st->grad2d.p,      st->tile_count.p,
                     st->tile_start.p, st->cursor.p,    st->order.p,     st->scan_part.p,   st->bucket,
                     st->keys.p,      st->keys_emit.p, st->det_partial.p, st->T_final.p,   st->n_last.p,
-                    st->twist_part.p, st->loss_part.p, st->ctr};
+                    st->twist_part.p, st->loss_part.p, st->occl.p,   st->cut.p,       st->ctr};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (st->ctr_host) cudaFreeHost(st->ctr_host);
@@ -445,6 +449,8 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
 
     CK(cudaMemsetAsync(st->tile_count.p, 0, (size_t)(NBK + 1) * sizeof(unsigned), s), "memset bucket counts");
     CK(cudaMemsetAsync(st->ctr, 0, sizeof(DevCounters), s), "memset counters");
+    const bool cut = !opt.full_lists;
+    if (cut) CK(cudaMemsetAsync(st->occl.p, 0, (size_t)NBK * sizeof(unsigned), s), "memset occlusion");
 
     ProjectArgs pa;
     pa.means = g->means; pa.log_scales = g->log_scales; pa.quats = g->quats;
@@ -452,9 +458,19 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     pa.n = n; pa.sh_degree = g->sh_degree; pa.near_z = opt.near_z; pa.guard = opt.guard_slope;
     pa.Tdev = T_cw_device;
     pa.rec = st->rec.p; pa.ext = st->ext.p; pa.vis_mask = st->vis_mask.p; pa.tile_count = st->tile_count.p;
+    pa.occl = cut ? st->occl.p : nullptr;
+    {
+        const int m = (opt.tile_w < opt.tile_h ? opt.tile_w : opt.tile_h) - 1;
+        pa.tile_fit = m * m / 4;
+    }
     {
         StageTimer tm(ctx, kStProject, s);
         CK(launch_project(pa, vb, s), "project");
+        if (cut) {
+            CutArgs ca;
+            ca.occl = st->occl.p; ca.tile_count = st->tile_count.p; ca.cut = st->cut.p; ca.n_tiles = T;
+            CK(launch_cut(ca, s), "cut");
+        }
     }
 
     ScanArgs sa;
@@ -485,6 +501,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     EmitArgs ea;
     ea.rec = st->rec.p; ea.ext = st->ext.p; ea.n = n; ea.cursor = st->cursor.p; ea.keys = st->keys_emit.p;
     ea.key_capacity = (unsigned long long)st->keys.cap; ea.ctr = st->ctr;
+    ea.cut = cut ? st->cut.p : nullptr;
     {
         StageTimer tm(ctx, kStEmit, s);
         CK(launch_emit(ea, vb, s), "emit");
@@ -628,6 +645,7 @@ s3gs_status render_bwd_impl(s3gs_ctx *ctx, s3gs_state *st, const float *d_rgb, c
         DetReduceArgs da;
         da.rec = st->rec.p; da.ext = st->ext.p; da.keys = st->keys.p; da.tile_start = st->tile_start.p;
         da.det_partial = st->det_partial.p; da.grad2d = st->grad2d.p; da.n = n;
+        da.cut = st->opt.full_lists ? nullptr : st->cut.p;
         StageTimer tm(ctx, kStDetReduce, s);
         CK(launch_det_reduce(da, vb, s), "det_reduce");
     }

@@ -208,12 +208,57 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
                 const unsigned hb = __shfl_sync(0xffffffffu, rowbase, src2);
                 kk[u] = __shfl_sync(0xffffffffu, rkey, src2);
                 pos[u] = 0xffffffffu;
-                if (j2 < tot2) pos[u] = atomicAdd(a.cursor + hb + (unsigned)(h0 + (int)(j2 - he)) * kDepthBins, 1u);
+                const unsigned bucket = hb + (unsigned)(h0 + (int)(j2 - he)) * kDepthBins;
+                // behind its tile's occlusion cut a pair is not listed
+                if (j2 < tot2 && (!a.cut || (bucket & (kDepthBins - 1)) <= a.cut[bucket / kDepthBins]))
+                    pos[u] = atomicAdd(a.cursor + bucket, 1u);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (pos[u] < a.key_capacity) a.keys[pos[u]] = kk[u];
         }
+    }
+}
+
+// ---- occlusion cut ----
+// One warp per tile: lane l holds depth bins 8l..8l+7 of the tile's optical-depth
+// sums; a warp scan finds the first bin at which the running sum reaches the
+// threshold. Bins behind it get a count of 0, so the scan, the emission and the
+// sort see only the bins some pixel of the tile can reach.
+__global__ void __launch_bounds__(256) cut_kernel(const CutArgs a) {
+    const long long t = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= a.n_tiles) return;
+    const int lane = threadIdx.x & 31;
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.occl + t * kDepthBins + lane * 8);
+    const uint4 w0 = src[0], w1 = src[1];
+    const unsigned o[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    unsigned long long run[8];
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) run[k] = (acc += o[k]);
+    unsigned long long incl = acc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const unsigned long long excl = incl - acc;
+    int first = kDepthBins - 1;
+#pragma unroll
+    for (int k = 7; k >= 0; --k)
+        if (excl + run[k] >= kOcclThreshold) first = lane * 8 + k;
+    const int b = (int)__reduce_min_sync(0xffffffffu, (unsigned)first);
+    if (lane == 0) a.cut[t] = (unsigned char)b;
+    if (b < kDepthBins - 1) {
+        uint4 *cnt = reinterpret_cast<uint4 *>(a.tile_count + t * kDepthBins + lane * 8);
+        const uint4 c0 = cnt[0], c1 = cnt[1];
+        const int b0 = lane * 8;
+        const uint4 n0 = make_uint4(b0 + 0 > b ? 0u : c0.x, b0 + 1 > b ? 0u : c0.y, b0 + 2 > b ? 0u : c0.z,
+                                    b0 + 3 > b ? 0u : c0.w);
+        const uint4 n1 = make_uint4(b0 + 4 > b ? 0u : c1.x, b0 + 5 > b ? 0u : c1.y, b0 + 6 > b ? 0u : c1.z,
+                                    b0 + 7 > b ? 0u : c1.w);
+        cnt[0] = n0;
+        cnt[1] = n1;
     }
 }
 
@@ -715,6 +760,12 @@ cudaError_t launch_scan(const ScanArgs &a, cudaStream_t s) {
 cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s) {
     if (vb.n_views == 0 || a.n == 0) return cudaSuccess;
     emit_kernel<<<dim3((unsigned)((a.n + 255) / 256), (unsigned)vb.n_views), 256, 0, s>>>(a, vb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cut(const CutArgs &a, cudaStream_t s) {
+    if (a.n_tiles == 0) return cudaSuccess;
+    cut_kernel<<<(unsigned)((a.n_tiles + 7) / 8), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -177,11 +177,19 @@ __device__ __forceinline__ float view_coord(const float *r, const float m[3], fl
 // fetches the record's cover ellipse with shuffles and computes the row's span of
 // covered tile columns (row_span). Level 2: a second scan numbers the round's
 // covered tiles, and in each sub-round every lane counts one. All lanes stay busy
-// whatever the mix of record sizes, and only covered tiles cost a count.
+// whatever the mix of record sizes, and only covered tiles cost a count. With the
+// occlusion cut on, a pair whose Gaussian can hold a whole tile also adds its
+// optical depth bound over that tile to the bucket (occl_units).
 __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const ViewBatch &vb, const ViewInfo &vi,
                                                  bool has, const CoverEllipse &ell, int tx0, int ty0, int ntx, int nty,
-                                                 int bin) {
-    const int lane = threadIdx.x & 31;
+                                                 int bin, const OcclGauss &og) {
+    __shared__ float4 s_og0[8][32], s_og1[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.occl) {
+        s_og0[warp][lane] = make_float4(og.u, og.v, og.a, og.b);
+        s_og1[warp][lane] = make_float4(og.c, og.thr, og.lo2, og.w);
+        __syncwarp();
+    }
     const unsigned nrows = has ? (unsigned)nty : 0u;
     const unsigned incl = warp_incl_scan(nrows);
     const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
@@ -197,9 +205,10 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
         const int s_ntx = __shfl_sync(0xffffffffu, ntx, src);
         const int s_bin = __shfl_sync(0xffffffffu, bin, src);
         int c0 = 0;
-        unsigned len = 0, rowbase = 0;
+        unsigned len = 0, rowbase = 0, rinfo = 0;
         if (j < total) {
             const int ty = (int)(s_t0 >> 16) + (int)(j - s_excl);
+            rinfo = (unsigned)src | ((unsigned)ty << 8);
             const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
             const int cx0 = (int)(s_t0 & 0xffffu);
             const int2 span = row_span(e, py0, py1, cx0, cx0 + s_ntx - 1, inv_tw);
@@ -216,7 +225,24 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
             const int h0 = __shfl_sync(0xffffffffu, c0, src2);
             const unsigned he = __shfl_sync(0xffffffffu, excl2, src2);
             const unsigned hb = __shfl_sync(0xffffffffu, rowbase, src2);
-            if (j2 < tot2) atomicAdd(a.tile_count + hb + (size_t)(h0 + (int)(j2 - he)) * kDepthBins, 1u);
+            const unsigned ri = __shfl_sync(0xffffffffu, rinfo, src2);
+            if (j2 < tot2) {
+                const int tx = h0 + (int)(j2 - he);
+                const size_t bucket = hb + (size_t)tx * kDepthBins;
+                atomicAdd(a.tile_count + bucket, 1u);
+                if (a.occl) {
+                    const float4 g1 = s_og1[warp][ri & 31u];
+                    if (g1.w > 0.f) {
+                        const float4 g0 = s_og0[warp][ri & 31u];
+                        const OcclGauss g = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                        const int ty = (int)(ri >> 8);
+                        const int x0 = tx * vb.tile_w, y0 = ty * vb.tile_h;
+                        const unsigned q = occl_units(g, (float)x0, (float)min(x0 + vb.tile_w - 1, vi.w - 1),
+                                                      (float)y0, (float)min(y0 + vb.tile_h - 1, vi.h - 1));
+                        if (q) atomicAdd(a.occl + bucket, q);
+                    }
+                }
+            }
         }
     }
 }
@@ -251,6 +277,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
         ell.u = ell.v = ell.B = ell.iA = ell.Aqc = ell.det = ell.yL = ell.mq = 0.f;
         ell.ym = -1.0f;
         int ctx0 = 0, cty0 = 0, cntx = 0, cnty = 0, cbin = 0;
+        OcclGauss og = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float T[12];
         load_pose(vi, a.Tdev, v, T);
         float px = view_coord(T, m, T[3]);
@@ -321,10 +348,19 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                     ell = cover_ellipse(u, vv, R.a.z, R.a.w, R.b.x, qc);
                     ctx0 = tx0; cty0 = ty0; cntx = tx1 - tx0 + 1; cnty = ty1 - ty0 + 1;
                     cbin = depth_bin(pz);
+                    if (a.occl) {
+                        // the blend's staged values (stage_record), and whether the
+                        // ellipse's inscribed disc is wide enough for a tile
+                        const StagedGauss sg = stage_record(R);
+                        og = {sg.u, sg.v, sg.a, sg.b, sg.c, sg.thr, sg.lo2, 0.f};
+                        const float ha = 0.5f * (R.a.z - R.b.x);
+                        const float lmax = 0.5f * (R.a.z + R.b.x) + sqrtf(ha * ha + R.a.w * R.a.w);
+                        og.w = qc >= lmax * (float)a.tile_fit ? 1.f : 0.f;
+                    }
                 }
             }
         }
-        count_cover_warp(a, vb, vi, has, ell, ctx0, cty0, cntx, cnty, cbin);
+        count_cover_warp(a, vb, vi, has, ell, ctx0, cty0, cntx, cnty, cbin, og);
         if (live) a.ext[r] = ext;
     }
     if (live) a.vis_mask[g] = mask;

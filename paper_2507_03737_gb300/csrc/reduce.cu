@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
     int ty0 = tile_of(y0 > 0.f ? (int)y0 : 0, vb.tile_h);
     int ty1 = tile_of(y1 < (float)(vi.h - 1) ? (int)y1 : vi.h - 1, vb.tile_h);
     const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | g;
+    const int bin = depth_bin(z);
     float acc[kGrad2d];
 #pragma unroll
     for (int q = 0; q < kGrad2d; ++q) acc[q] = 0.f;
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const DetReduceArgs a, 
         const int2 span = row_span(ell, py0, py1, tx0, tx1, inv_tw);  // the tiles the record is listed in
         for (int tx = span.x; tx <= span.y; ++tx) {
             int t = vi.tile_base + ty * vi.tiles_x + tx;
+            if (a.cut && bin > (int)a.cut[t]) continue;  // behind the tile's occlusion cut: not listed
             unsigned lo = a.tile_start[t * kDepthBins], hi = a.tile_start[(t + 1) * kDepthBins];
             while (lo < hi) {
                 unsigned mid = lo + ((hi - lo) >> 1);

@@ -326,6 +326,54 @@ __device__ __forceinline__ float pair_alpha(const PairEval &e) { return e.clampe
 
 __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }
 
+// ---- occlusion cut ----
+// Eq. 2 composites a pixel front to back and stops at the first Gaussian that
+// would take the transmittance below 1e-4. If the Gaussians of a tile's depth bins
+// 0..b are certain to drive every pixel of the tile below that level, no pixel
+// reaches bin b + 1, and the tile's list can end after bin b without changing any
+// output or gradient. The certainty comes from Gaussians that cover the whole tile:
+// for such a Gaussian the alpha of every pixel is at least alpha_min (below), so
+// every pixel's transmittance after bins 0..b is at most exp(-sum of -ln(1 -
+// alpha_min)). Each covered (Gaussian, tile) pair adds its optical depth -ln(1 -
+// alpha_min), rounded down in fixed point, to its (tile, depth bin) bucket; the cut
+// is the first bin at which the tile's running sum reaches ln(1e4) plus a margin.
+constexpr float kOcclScale = 65536.0f;  // fixed-point units per nat
+// ln(1e4) + 1e-3 in units: exp(-(ln(1e4) + 1e-3)) is below the FP32 constant 1e-4f
+constexpr unsigned kOcclThreshold = 603675u;
+
+struct OcclGauss {
+    float u, v, a, b;      // centre and scaled conic as staged by the blend (see stage_record)
+    float c, thr, lo2, w;  // w > 0: the ellipse can hold a whole tile
+};
+
+// Optical depth lower bound of one Gaussian over the pixel centres [x0, x1] x [y0, y1]
+// of a tile, in fixed-point units (0 if some pixel may cut or skip it). The blend
+// computes p = a dx^2 + b dx dy + c dy^2 in FP32; in exact arithmetic p is concave
+// (the conic is positive definite), so over the rectangle its minimum is at a corner.
+// The FP32 error of the blend's evaluation at any pixel and of the evaluation here
+// at the corners is below 20 ulp of M = |a| dx^2 + |b dx dy| + |c| dy^2 taken at the
+// farthest extents; p is lowered by M 2^-18. alpha, -ln(1 - alpha) and the rounding
+// of each transmittance product (a factor of at most (1 + 2^-24)^2 per blended
+// Gaussian) are then covered by relative margins and one unit taken off each pair.
+__device__ __forceinline__ unsigned occl_units(const OcclGauss &g, float x0, float x1, float y0, float y1) {
+    const float dx0 = __fsub_rn(x0, g.u), dx1 = __fsub_rn(x1, g.u);
+    const float dy0 = __fsub_rn(y0, g.v), dy1 = __fsub_rn(y1, g.v);
+    const float ax0 = g.a * dx0 * dx0, ax1 = g.a * dx1 * dx1;
+    const float cy0 = g.c * dy0 * dy0, cy1 = g.c * dy1 * dy1;
+    const float bx0 = g.b * dx0, bx1 = g.b * dx1;
+    const float pmin = fminf(fminf(fmaf(bx0, dy0, ax0 + cy0), fmaf(bx1, dy0, ax1 + cy0)),
+                             fminf(fmaf(bx0, dy1, ax0 + cy1), fmaf(bx1, dy1, ax1 + cy1)));
+    const float mx = fmaxf(fabsf(dx0), fabsf(dx1)), my = fmaxf(fabsf(dy0), fabsf(dy1));
+    const float M = fabsf(g.a) * mx * mx + fabsf(g.b) * mx * my + fabsf(g.c) * my * my;
+    const float plo = pmin - M * 3.814697265625e-6f - 1e-6f;  // 2^-18
+    if (!(plo >= g.thr)) return 0u;
+    const float l = plo + g.lo2 - 1e-5f;
+    const float alpha = (l >= kClampL ? kAlphaMax : exp2f(l)) * (1.0f - 1e-5f);
+    const float od = -log1pf(-alpha) * (1.0f - 1e-5f);
+    const unsigned q = (unsigned)(od * kOcclScale);  // truncation rounds down
+    return q > 0u ? q - 1u : 0u;
+}
+
 // ---- launch wrappers (one per translation unit) ----
 struct ProjectArgs {
     const float *means, *log_scales, *quats, *opacity_logits, *colors;
@@ -338,8 +386,20 @@ struct ProjectArgs {
     int2 *ext;
     unsigned *vis_mask;  // [n]: bit v set if the Gaussian is projected into view v
     unsigned *tile_count;
+    unsigned *occl;      // per bucket optical depth lower bound (see occl_units); null: no cut
+    int tile_fit;        // (min(tile_w, tile_h) - 1)^2 / 4: squared inradius a tile needs
 };
 cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s);
+
+// Per tile: the last depth bin its list keeps (255: all), and the counts of the
+// bins behind it set to 0 before the scan.
+struct CutArgs {
+    const unsigned *occl;
+    unsigned *tile_count;
+    unsigned char *cut;
+    long long n_tiles;
+};
+cudaError_t launch_cut(const CutArgs &a, cudaStream_t s);
 
 struct ScanArgs {
     const unsigned *tile_count;  // per bucket
@@ -360,6 +420,7 @@ struct EmitArgs {
     unsigned long long *keys;
     unsigned long long key_capacity;
     const DevCounters *ctr;
+    const unsigned char *cut;  // per tile last kept depth bin; null: keep all
 };
 cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s);
 
@@ -421,6 +482,7 @@ struct DetReduceArgs {
     const float *det_partial;
     float *grad2d;
     long long n;
+    const unsigned char *cut;  // per tile last kept depth bin; null: keep all
 };
 cudaError_t launch_det_reduce(const DetReduceArgs &a, const ViewBatch &vb, cudaStream_t s);
 

@@ -47,7 +47,7 @@ def test_host_only_calls(lib):
     assert b"sm_103a" in lib.s3gs_version()
     from paper_2507_03737_gb300 import binding as B
     o = B.s3gs_options_default()
-    assert (o.tile_w, o.tile_h, o.auto_grow) == (16, 16, 1)
+    assert (o.tile_w, o.tile_h, o.auto_grow, o.full_lists) == (16, 16, 1, 0)
     assert abs(o.near_z - 0.2) < 1e-7
     # null arguments are rejected without touching the GPU
     assert lib.s3gs_create(0, None) == B.S3GS_E_INVALID
@@ -56,7 +56,8 @@ def test_host_only_calls(lib):
 def test_binding_struct_layout_matches_header():
     from paper_2507_03737_gb300 import binding as B
     assert ctypes.sizeof(B.Camera) == 4 * (2 + 4 + 12)
-    assert ctypes.sizeof(B.Options) == 4 * (9 + 2 + 3)
+    assert ctypes.sizeof(B.Options) == 4 * (9 + 2 + 3 + 1)
+    assert B.Options.full_lists.offset == 4 * (9 + 2 + 3)
     assert B.Gaussians.means.offset == 16
 
 

@@ -72,7 +72,7 @@ CASES = [("config1", (16, 16)), ("config1", (8, 8)), ("config1", (32, 8)), ("rag
 def test_cover_lists_every_contributing_pair(R, name, tile):
     from paper_2507_03737_gb300 import binding as B
     sc = _case(name)
-    R.render_np(sc, options=B.s3gs_options_default(tile_w=tile[0], tile_h=tile[1]))
+    R.render_np(sc, options=B.s3gs_options_default(tile_w=tile[0], tile_h=tile[1], full_lists=1))
     keys, vals, _ = B.s3gs_debug_binning(R.ctx, R.state)
     res = check_cover(sc, sc.cameras, listed_pairs(keys, vals), tile[0], tile[1])
     print(f"COVER {name} {tile[0]}x{tile[1]}: {res}")

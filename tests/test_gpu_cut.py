@@ -1,0 +1,136 @@
+"""The occlusion cut changes no output and no gradient (GPU).
+
+Eq. 2 stops compositing a pixel at the first Gaussian that would take its
+transmittance below 1e-4. By default the library ends each tile's list after the
+first depth bin by which the Gaussians that cover the whole tile are certain, by a
+bound with FP32 margins, to have stopped every pixel of the tile. Each scene here
+is rendered with the cut and with every covered pair listed (full_lists = 1; that
+list is pinned bit for bit against the integer referee by the binning tests), and:
+
+- each tile's list with the cut is a prefix of its full list that ends at a
+  depth-bin boundary;
+- rgb, depth, pointmap and alpha are bitwise equal;
+- in deterministic mode every gradient tensor, the twist included, is bitwise equal;
+- on the large-Gaussian workload the cut removes most of the list, so the
+  comparison is not vacuous.
+"""
+import numpy as np
+import pytest
+
+from paper_2507_03737_gb300 import scenes
+from tests.gpu_helpers import upstream
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2507_03737_gb300.autograd import Renderer
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def _depth_bin(depth_bits):
+    """The renderer's log-depth bin of a depth given by its FP32 bit pattern."""
+    b = (depth_bits.astype(np.int64) >> 19) - 1993
+    return np.clip(b, 0, 255)
+
+
+def _case(name):
+    if name == "config1":
+        return scenes.config_scene(1)
+    if name == "config3_200k_2views":
+        sc = scenes.config_scene(3, n_override=200_000)
+        sc.cameras = sc.cameras[:2]
+        return sc
+    if name == "config5_2views":
+        # 5M large, elongated SH-3 Gaussians; one view of each size
+        sc = scenes.config_scene(5)
+        sc.cameras = sc.cameras[:2]
+        return sc
+    if name == "opaque_wall":
+        # a wall of opaque, wide Gaussians in front of a cloud of small ones: most
+        # tiles are cut after the wall's depth bins
+        rng = np.random.default_rng(11)
+        n_wall, n_back = 3000, 200000
+        wall = np.stack([rng.uniform(-3, 3, n_wall), rng.uniform(-2, 2, n_wall), rng.uniform(3.0, 3.2, n_wall)], 1)
+        back = np.stack([rng.uniform(-4, 4, n_back), rng.uniform(-3, 3, n_back), rng.uniform(4, 12, n_back)], 1)
+        sc = scenes.random_gaussians(rng, np.concatenate([wall, back]), 1)
+        sc.log_scales[:n_wall] = np.log(0.25).astype(np.float32)
+        sc.opacity_logits[:n_wall] = 3.0
+        sc.cameras = [scenes.camera(160, 120, 150.0, 150.0, 80.0, 60.0),
+                      scenes.camera(97, 61, 90.0, 90.0, 40.0, 33.0)]
+        return sc
+    raise ValueError(name)
+
+
+def _lists(R, sc, **kw):
+    from paper_2507_03737_gb300 import binding as B
+    out = R.render_np(sc, options=B.s3gs_options_default(**kw))
+    keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
+    return out, keys.copy(), vals.copy(), ranges.copy()
+
+
+def _check_prefix(keys, vals, ranges, fkeys, fvals, franges):
+    n = np.diff(ranges)
+    nf = np.diff(franges)
+    assert np.all(n <= nf)
+    tile = np.repeat(np.arange(n.size), n)
+    off = np.arange(keys.size) - np.repeat(ranges[:-1], n)
+    src = franges[:-1][tile] + off
+    assert np.array_equal(keys, fkeys[src]) and np.array_equal(vals, fvals[src])
+    # where a tile's list was cut, the first dropped key lies in a later depth bin
+    # than the last kept one
+    cut = np.nonzero((n < nf) & (n > 0))[0]
+    last = _depth_bin(fkeys[franges[cut] + n[cut] - 1] & 0xffffffff)
+    nxt = _depth_bin(fkeys[franges[cut] + n[cut]] & 0xffffffff)
+    assert np.all(nxt > last)
+    return int(np.count_nonzero(n < nf))
+
+
+CASES = ["config1", "opaque_wall", "config3_200k_2views", "config5_2views"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_cut_lists_are_prefixes_and_outputs_are_unchanged(R, name):
+    sc = _case(name)
+    full, fkeys, fvals, franges = _lists(R, sc, full_lists=1)
+    cut, keys, vals, ranges = _lists(R, sc)
+    n_cut_tiles = _check_prefix(keys, vals, ranges, fkeys, fvals, franges)
+    for k in full:
+        assert np.array_equal(full[k].view(np.uint32), cut[k].view(np.uint32)), k
+    kept = keys.size / max(fkeys.size, 1)
+    print(f"CUT {name}: kept {keys.size} of {fkeys.size} pairs ({kept:.4f}); tiles cut {n_cut_tiles} of "
+          f"{ranges.size - 1}")
+    if name in ("opaque_wall", "config5_2views"):
+        assert kept < 0.5, kept
+    if name == "config5_2views":
+        assert kept < 0.1, kept
+
+
+@pytest.mark.parametrize("name", ["opaque_wall", "config3_200k_2views", "config5_2views"])
+def test_cut_gradients_are_bitwise_unchanged(R, name):
+    sc = _case(name)
+    V = len(sc.cameras)
+    ups = upstream(sc.cameras, 7)
+    res = {}
+    for fl in (1, 0):
+        _lists(R, sc, full_lists=fl, deterministic=1)
+        res[fl] = R.backward_np(ups, V)
+    for k in res[1]:
+        assert np.array_equal(res[1][k].view(np.uint32), res[0][k].view(np.uint32)), k
+
+
+def test_cut_with_recompute_and_persistent_grid(R):
+    """The recompute replay and the persistent grid read the same cut lists."""
+    sc = _case("opaque_wall")
+    ups = upstream(sc.cameras, 3)
+    res = {}
+    for fl in (1, 0):
+        _lists(R, sc, full_lists=fl, deterministic=1, recompute=1, blocks_per_sm=4)
+        res[fl] = R.backward_np(ups, len(sc.cameras))
+    for k in res[1]:
+        assert np.array_equal(res[1][k].view(np.uint32), res[0][k].view(np.uint32)), k

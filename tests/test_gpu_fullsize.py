@@ -238,7 +238,7 @@ def test_config3_binning_bit_exact_at_full_size(R):
     integer referee's stable sort of the same records' cover, bit for bit."""
     from paper_2507_03737_gb300 import binding as B
     sc = scenes.config_scene(3)
-    R.render_np(sc)
+    R.render_np(sc, options=B.s3gs_options_default(full_lists=1))
     V = len(sc.cameras)
     rec = B.s3gs_debug_records(R.ctx, R.state, V * sc.n)
     qc = B.s3gs_debug_cover(R.ctx, R.state, V * sc.n)

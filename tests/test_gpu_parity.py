@@ -57,7 +57,7 @@ def test_binning_bit_exact(R, tile):
     sc = scenes.tiny_scene(5, n=300, width=77, height=45, n_views=3, scale=0.2)
     sc.cameras[1] = dict(sc.cameras[1], width=33, height=70)
     sc.cameras[2] = dict(sc.cameras[2], width=16, height=16)
-    opt = _opts(tile_w=tile[0], tile_h=tile[1])
+    opt = _opts(tile_w=tile[0], tile_h=tile[1], full_lists=1)
     R.render_np(sc, options=opt)
     rec = B.s3gs_debug_records(R.ctx, R.state, sc.n * 3)
     keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
@@ -237,7 +237,7 @@ def test_heavy_tile_sort_path(R):
     sc = scenes.random_gaussians(rng, means, 0, np.log(0.01), 0.3)
     sc.opacity_logits[:] = -4.0  # keep pixels from saturating so every duplicate is reached
     sc.cameras = [scenes.camera(32, 32, 40.0, 40.0, 15.5, 15.5)]
-    gpu = R.render_np(sc)
+    gpu = R.render_np(sc, options=_opts(full_lists=1))
     keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
     assert np.diff(ranges).max() > 4096
     rec = B.s3gs_debug_records(R.ctx, R.state, n)
@@ -264,7 +264,7 @@ def test_equal_depth_stacks_sort_exactly(R, n_same, n_rest):
     perm = rng.permutation(n)  # interleave the stack with the others in index order
     sc = scenes.random_gaussians(rng, means[perm], 0, np.log(0.01), 0.3)
     sc.cameras = [scenes.camera(32, 32, 40.0, 40.0, 15.5, 15.5)]
-    R.render_np(sc)
+    R.render_np(sc, options=_opts(full_lists=1))
     keys, vals, ranges = B.s3gs_debug_binning(R.ctx, R.state)
     rec = B.s3gs_debug_records(R.ctx, R.state, n)
     qc = B.s3gs_debug_cover(R.ctx, R.state, n)
