@@ -38,10 +38,12 @@ FP32_LANES_PER_SM = 128
 # the committed ncu summaries profile, the same kernels: config 3 runs a persistent
 # heaviest-first grid of 12 CTAs per SM, 2 pixels per forward and 4 per backward
 # blend thread, batches of 128 staged Gaussians; the small single view of config 1
-# fills the GPU only with 8x8 tiles of one pixel per thread.
+# fills the GPU only with 8x8 tiles of one pixel per thread. Neither has a tile whose
+# front Gaussians cover it opaquely, so both list every covered pair (the occlusion
+# cut would only add its optical-depth pass).
 TUNED_SCHEDULES = {
-    1: {"tile_w": 8, "tile_h": 8, "pixels_per_thread": 1, "bwd_pixels_per_thread": 1, "batch": 64},
-    3: {"blocks_per_sm": 12, "pixels_per_thread": 2, "bwd_pixels_per_thread": 4, "batch": 128},
+    1: {"tile_w": 8, "tile_h": 8, "pixels_per_thread": 1, "bwd_pixels_per_thread": 1, "batch": 64, "full_lists": 1},
+    3: {"blocks_per_sm": 12, "pixels_per_thread": 2, "bwd_pixels_per_thread": 4, "batch": 128, "full_lists": 1},
 }
 # blend schedule of the mapping-iteration row (run_mapping says how it was chosen)
 MAPPING_SCHEDULE = {"blocks_per_sm": 8, "pixels_per_thread": 2, "bwd_pixels_per_thread": 2}
@@ -64,6 +66,9 @@ def parse():
     ap.add_argument("--deterministic", type=int, default=0)
     ap.add_argument("--recompute", type=int, default=-1, help="1 = recompute the blend state in the backward "
                     "(default: on for config 5 only)")
+    ap.add_argument("--full-lists", type=int, default=-1,
+                    help="1 = list every covered (tile, Gaussian) pair, 0 = occlusion cut (default: the "
+                         "workload's schedule, else the library default, the cut)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -415,6 +420,9 @@ def run_native(args):
         for k, v in options_to_dict(best).items():
             setattr(wl.opt, k, v)
         tuned = options_to_dict(best)
+    if args.full_lists >= 0:
+        wl.opt.full_lists = args.full_lists
+        tuned = dict(tuned or {}, full_lists=args.full_lists)
 
     # size every buffer (auto-grow), then switch to the no-sync capture-safe mode
     wl.step_batched()

@@ -1,9 +1,11 @@
 """Autotuner of the blend schedule: tile shape, pixels per thread (forward and
-backward), Gaussians staged per batch and the persistent-grid size.
+backward), Gaussians staged per batch, the persistent-grid size and whether the
+tile lists take the occlusion cut.
 
 None of these choices changes forward results (the per-pixel 3-sigma test is
-explicit, so tiles are only a conservative cover); they change only the
-summation order of atomically accumulated gradients. The tuner times a
+explicit, so tiles are only a conservative cover, and the occlusion cut drops only
+pairs no pixel reaches); they change only the summation order of atomically
+accumulated gradients. The tuner times a
 forward + backward of the caller's own workload with CUDA events and keeps the
 fastest option set, by coordinate descent from the caller's base schedule (the
 library defaults unless one is given). Results
@@ -27,8 +29,9 @@ SEARCH_SPACE = {
     "bwd_pixels_per_thread": [1, 2, 4],
     "batch": [64, 128, 256, 512],
     "blocks_per_sm": [0, 2, 4, 8, 12, 16],
+    "full_lists": [0, 1],
 }
-FIELDS = ("tile_w", "tile_h", "pixels_per_thread", "bwd_pixels_per_thread", "batch", "blocks_per_sm")
+FIELDS = ("tile_w", "tile_h", "pixels_per_thread", "bwd_pixels_per_thread", "batch", "blocks_per_sm", "full_lists")
 
 
 def options_to_dict(o: B.Options) -> dict:

@@ -72,6 +72,7 @@ struct s3gs_state {
     DevBuf<unsigned> tile_count, tile_start, cursor, order, scan_part;
     DevBuf<unsigned> occl;        // per bucket optical depth lower bound (occlusion cut)
     DevBuf<unsigned char> cut;    // per tile last listed depth bin
+    DevBuf<unsigned> cut_max;     // [tiles] row maxima of the cut (at row starts), then [32] view maxima
     DevBuf<unsigned long long> keys;       // tile-sorted duplicate list
     DevBuf<unsigned long long> keys_emit;  // emission order, read by the tile sort
     DevBuf<float> det_partial;
@@ -244,6 +245,7 @@ s3gs_status ensure_forward_buffers(s3gs_ctx *ctx, s3gs_state *st, long long n_re
     if ((r = grow(ctx, st->scan_part, (n_buckets + 4095) / 4096 + 2, s, "scan_part")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->occl, n_buckets + 1, s, "occlusion")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->cut, n_tiles + 16, s, "cut")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->cut_max, n_tiles + S3GS_MAX_VIEWS, s, "cut_max")) != S3GS_OK) return r;
     if (store) {
         if ((r = grow(ctx, st->T_final, n_pix, s, "T_final")) != S3GS_OK) return r;
         if ((r = grow(ctx, st->n_last, n_pix, s, "n_last")) != S3GS_OK) return r;
@@ -376,7 +378,8 @@ void s3gs_state_destroy(s3gs_state *st) {
     void *bufs[] = {st->rec.p,       st->ext.p,       st->vis_mask.p,  st->grad2d.p,      st->tile_count.p,
                     st->tile_start.p, st->cursor.p,    st->order.p,     st->scan_part.p,   st->bucket,
                     st->keys.p,      st->keys_emit.p, st->det_partial.p, st->T_final.p,   st->n_last.p,
-                    st->twist_part.p, st->loss_part.p, st->occl.p,   st->cut.p,       st->ctr};
+                    st->twist_part.p, st->loss_part.p, st->occl.p,   st->cut.p,       st->cut_max.p,
+                    st->ctr};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (st->ctr_host) cudaFreeHost(st->ctr_host);
@@ -450,7 +453,10 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     CK(cudaMemsetAsync(st->tile_count.p, 0, (size_t)(NBK + 1) * sizeof(unsigned), s), "memset bucket counts");
     CK(cudaMemsetAsync(st->ctr, 0, sizeof(DevCounters), s), "memset counters");
     const bool cut = !opt.full_lists;
-    if (cut) CK(cudaMemsetAsync(st->occl.p, 0, (size_t)NBK * sizeof(unsigned), s), "memset occlusion");
+    if (cut) {
+        CK(cudaMemsetAsync(st->occl.p, 0, (size_t)NBK * sizeof(unsigned), s), "memset occlusion");
+        CK(cudaMemsetAsync(st->cut_max.p, 0, (size_t)(T + S3GS_MAX_VIEWS) * sizeof(unsigned), s), "memset cut maxima");
+    }
 
     ProjectArgs pa;
     pa.means = g->means; pa.log_scales = g->log_scales; pa.quats = g->quats;
@@ -463,13 +469,21 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
         const int m = (opt.tile_w < opt.tile_h ? opt.tile_w : opt.tile_h) - 1;
         pa.tile_fit = m * m / 4;
     }
+    EmitArgs ea;
+    ea.rec = st->rec.p; ea.ext = st->ext.p; ea.n = n; ea.cursor = st->cursor.p; ea.keys = nullptr;
+    ea.key_capacity = 0; ea.ctr = st->ctr; ea.tile_count = st->tile_count.p;
+    ea.cut = cut ? st->cut.p : nullptr;
+    ea.row_max = st->cut_max.p; ea.view_max = st->cut_max.p + T;
     {
+        // with the cut: projection and optical depths, the cut, then the bucket counts
         StageTimer tm(ctx, kStProject, s);
         CK(launch_project(pa, vb, s), "project");
         if (cut) {
             CutArgs ca;
-            ca.occl = st->occl.p; ca.tile_count = st->tile_count.p; ca.cut = st->cut.p; ca.n_tiles = T;
-            CK(launch_cut(ca, s), "cut");
+            ca.occl = st->occl.p; ca.cut = st->cut.p; ca.n_tiles = T;
+            ca.row_max = st->cut_max.p; ca.view_max = st->cut_max.p + T;
+            CK(launch_cut(ca, vb, s), "cut");
+            CK(launch_count(ea, vb, s), "count");
         }
     }
 
@@ -498,10 +512,8 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
         if ((r = grow(ctx, st->det_partial, st->keys.cap * kGrad2d, s, "det_partial")) != S3GS_OK) return r;
     }
 
-    EmitArgs ea;
-    ea.rec = st->rec.p; ea.ext = st->ext.p; ea.n = n; ea.cursor = st->cursor.p; ea.keys = st->keys_emit.p;
-    ea.key_capacity = (unsigned long long)st->keys.cap; ea.ctr = st->ctr;
-    ea.cut = cut ? st->cut.p : nullptr;
+    ea.keys = st->keys_emit.p;  // the duplicate buffers may have grown since the count
+    ea.key_capacity = (unsigned long long)st->keys.cap;
     {
         StageTimer tm(ctx, kStEmit, s);
         CK(launch_emit(ea, vb, s), "emit");

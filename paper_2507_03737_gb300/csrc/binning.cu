@@ -122,11 +122,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const ScanArgs a) {
 // stay busy whatever the mix of visible, culled, small and large records, and
 // only covered tiles cost a cursor atomic. Four sub-rounds of cursor atomics
 // are issued before their results are consumed.
+//
+// With the occlusion cut the same enumeration first runs in COUNT mode (after the
+// cut, before the scan), counting only the pairs in front of their tile's cut. A
+// record behind its view's largest cut is skipped whole, a row behind the row's
+// largest cut costs no level-2 work, and each pair is checked against its tile's cut.
+template <bool COUNT>
 __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __grid_constant__ ViewBatch vb) {
     __shared__ unsigned s_incl[8][32], s_excl[8][32], s_t0[8][32], s_ntx[8][32], s_orig[8][32];
     __shared__ unsigned long long s_key[8][32];
     __shared__ CoverEllipse s_ell[8][32];  // cover ellipse of the source record
-    if (a.ctr->overflow) return;
+    if (!COUNT && a.ctr->overflow) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // blockIdx.y is the view, so no record index needs dividing
     const int v = (int)blockIdx.y;
@@ -140,10 +146,11 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
     ell.ym = -1.0f;
     if (gl < a.n) {
         const int2 ext = a.ext[r];
-        if (ext.x > 0) {
+        const float4 rb = ext.x > 0 ? a.rec[r].b : make_float4(0.f, 0.f, 0.f, 0.f);
+        // a record behind every cut of its view lists nowhere
+        if (ext.x > 0 && !(a.cut && (unsigned)depth_bin(rb.z) > a.view_max[v])) {
             const unsigned g = (unsigned)gl;
             const float4 ra = a.rec[r].a;
-            const float4 rb = a.rec[r].b;
             const float z = rb.z;
             ell = cover_ellipse(ra.x, ra.y, ra.z, ra.w, rb.x, a.rec[r].c.w);
             const float x0 = ceilf(__fsub_rn(ra.x, (float)ext.x)), x1 = floorf(__fadd_rn(ra.x, (float)ext.x));
@@ -183,19 +190,35 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
             for (unsigned b = 16; b > 0; b >>= 1)
                 if (s_incl[warp][src + b - 1] <= j) src += b;
             const unsigned row = j - s_excl[warp][src];
-            const unsigned tt = s_t0[warp][src];
-            const int ty = (int)(tt >> 16) + (int)row;
-            const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
-            const int cx0 = (int)(tt & 0xffffu);
-            const int2 span = row_span(s_ell[warp][src], py0, py1, cx0, cx0 + (int)s_ntx[warp][src] - 1, inv_tw);
-            c0 = span.x;
-            len = span.y >= span.x ? (unsigned)(span.y - span.x + 1) : 0u;
             rowbase = s_orig[warp][src] + row * row_stride;
-            rkey = s_key[warp][src];
+            // the row's largest cut sits at its first tile
+            if (!a.cut || (rowbase & (kDepthBins - 1)) <= a.row_max[rowbase / kDepthBins]) {
+                const unsigned tt = s_t0[warp][src];
+                const int ty = (int)(tt >> 16) + (int)row;
+                const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
+                const int cx0 = (int)(tt & 0xffffu);
+                const int2 span = row_span(s_ell[warp][src], py0, py1, cx0, cx0 + (int)s_ntx[warp][src] - 1, inv_tw);
+                c0 = span.x;
+                len = span.y >= span.x ? (unsigned)(span.y - span.x + 1) : 0u;
+                rkey = s_key[warp][src];
+            }
         }
         const unsigned incl2 = warp_incl_scan(len);
         const unsigned tot2 = __shfl_sync(0xffffffffu, incl2, 31);
         const unsigned excl2 = incl2 - len;
+        if (COUNT) {
+            for (unsigned b2 = 0; b2 < tot2; b2 += 32) {
+                const unsigned j2 = b2 + lane;
+                const int src2 = warp_find(incl2, j2);
+                const int h0 = __shfl_sync(0xffffffffu, c0, src2);
+                const unsigned he = __shfl_sync(0xffffffffu, excl2, src2);
+                const unsigned hb = __shfl_sync(0xffffffffu, rowbase, src2);
+                const unsigned bucket = hb + (unsigned)(h0 + (int)(j2 - he)) * kDepthBins;
+                if (j2 < tot2 && (bucket & (kDepthBins - 1)) <= a.cut[bucket / kDepthBins])
+                    atomicAdd(a.tile_count + bucket, 1u);
+            }
+            continue;
+        }
         for (unsigned b2 = 0; b2 < tot2; b2 += 4 * 32) {
             unsigned pos[4];
             unsigned long long kk[4];
@@ -223,9 +246,11 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
 // ---- occlusion cut ----
 // One warp per tile: lane l holds depth bins 8l..8l+7 of the tile's optical-depth
 // sums; a warp scan finds the first bin at which the running sum reaches the
-// threshold. Bins behind it get a count of 0, so the scan, the emission and the
-// sort see only the bins some pixel of the tile can reach.
-__global__ void __launch_bounds__(256) cut_kernel(const CutArgs a) {
+// threshold, which is the last bin the tile lists. Its largest value over each tile
+// row is kept at the row's first tile (row_max) and over each view (view_max), both
+// zeroed before, so the count and the emission can pass over whole rows and records
+// that lie behind every cut they could meet.
+__global__ void __launch_bounds__(256) cut_kernel(const CutArgs a, const __grid_constant__ ViewBatch vb) {
     const long long t = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= a.n_tiles) return;
     const int lane = threadIdx.x & 31;
@@ -247,18 +272,15 @@ __global__ void __launch_bounds__(256) cut_kernel(const CutArgs a) {
 #pragma unroll
     for (int k = 7; k >= 0; --k)
         if (excl + run[k] >= kOcclThreshold) first = lane * 8 + k;
-    const int b = (int)__reduce_min_sync(0xffffffffu, (unsigned)first);
-    if (lane == 0) a.cut[t] = (unsigned char)b;
-    if (b < kDepthBins - 1) {
-        uint4 *cnt = reinterpret_cast<uint4 *>(a.tile_count + t * kDepthBins + lane * 8);
-        const uint4 c0 = cnt[0], c1 = cnt[1];
-        const int b0 = lane * 8;
-        const uint4 n0 = make_uint4(b0 + 0 > b ? 0u : c0.x, b0 + 1 > b ? 0u : c0.y, b0 + 2 > b ? 0u : c0.z,
-                                    b0 + 3 > b ? 0u : c0.w);
-        const uint4 n1 = make_uint4(b0 + 4 > b ? 0u : c1.x, b0 + 5 > b ? 0u : c1.y, b0 + 6 > b ? 0u : c1.z,
-                                    b0 + 7 > b ? 0u : c1.w);
-        cnt[0] = n0;
-        cnt[1] = n1;
+    const unsigned b = __reduce_min_sync(0xffffffffu, (unsigned)first);
+    if (lane == 0) {
+        a.cut[t] = (unsigned char)b;
+        int v = 0;
+        while (v + 1 < vb.n_views && vb.v[v + 1].tile_base <= t) ++v;
+        const ViewInfo &vi = vb.v[v];
+        const int ty = (int)(t - vi.tile_base) / vi.tiles_x;
+        atomicMax(a.row_max + vi.tile_base + ty * vi.tiles_x, b);
+        atomicMax(a.view_max + v, b);
     }
 }
 
@@ -759,13 +781,19 @@ cudaError_t launch_scan(const ScanArgs &a, cudaStream_t s) {
 
 cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s) {
     if (vb.n_views == 0 || a.n == 0) return cudaSuccess;
-    emit_kernel<<<dim3((unsigned)((a.n + 255) / 256), (unsigned)vb.n_views), 256, 0, s>>>(a, vb);
+    emit_kernel<false><<<dim3((unsigned)((a.n + 255) / 256), (unsigned)vb.n_views), 256, 0, s>>>(a, vb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cut(const CutArgs &a, cudaStream_t s) {
+cudaError_t launch_count(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s) {
+    if (vb.n_views == 0 || a.n == 0) return cudaSuccess;
+    emit_kernel<true><<<dim3((unsigned)((a.n + 255) / 256), (unsigned)vb.n_views), 256, 0, s>>>(a, vb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cut(const CutArgs &a, const ViewBatch &vb, cudaStream_t s) {
     if (a.n_tiles == 0) return cudaSuccess;
-    cut_kernel<<<(unsigned)((a.n_tiles + 7) / 8), 256, 0, s>>>(a);
+    cut_kernel<<<(unsigned)((a.n_tiles + 7) / 8), 256, 0, s>>>(a, vb);
     return cudaGetLastError();
 }
 

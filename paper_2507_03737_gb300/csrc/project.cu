@@ -178,8 +178,9 @@ __device__ __forceinline__ float view_coord(const float *r, const float m[3], fl
 // covered tile columns (row_span). Level 2: a second scan numbers the round's
 // covered tiles, and in each sub-round every lane counts one. All lanes stay busy
 // whatever the mix of record sizes, and only covered tiles cost a count. With the
-// occlusion cut on, a pair whose Gaussian can hold a whole tile also adds its
-// optical depth bound over that tile to the bucket (occl_units).
+// occlusion cut on, the bucket counts are made later (after the cut) and this pass
+// takes only the records that can hold a whole tile: each of their pairs adds its
+// optical depth bound over the tile to the bucket (occl_units).
 __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const ViewBatch &vb, const ViewInfo &vi,
                                                  bool has, const CoverEllipse &ell, int tx0, int ty0, int ntx, int nty,
                                                  int bin, const OcclGauss &og) {
@@ -190,7 +191,7 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
         s_og1[warp][lane] = make_float4(og.c, og.thr, og.lo2, og.w);
         __syncwarp();
     }
-    const unsigned nrows = has ? (unsigned)nty : 0u;
+    const unsigned nrows = (has && (!a.occl || og.w > 0.f)) ? (unsigned)nty : 0u;
     const unsigned incl = warp_incl_scan(nrows);
     const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
     const unsigned excl = incl - nrows;
@@ -211,7 +212,16 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
             rinfo = (unsigned)src | ((unsigned)ty << 8);
             const int py0 = ty * vb.tile_h, py1 = min(py0 + vb.tile_h - 1, vi.h - 1);
             const int cx0 = (int)(s_t0 & 0xffffu);
-            const int2 span = row_span(e, py0, py1, cx0, cx0 + s_ntx - 1, inv_tw);
+            int2 span;
+            if (a.occl) {
+                // only tiles inside the ellipse where alpha >= kOcclAlpha can add
+                const float4 g0 = s_og0[warp][src], g1 = s_og1[warp][src];
+                const OcclGauss g = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                span = strong_span(g, fmaxf(g.thr, kOcclLog2Alpha - g.lo2), py0, py1, cx0, cx0 + s_ntx - 1,
+                                   vb.tile_w, vi.w);
+            } else {
+                span = row_span(e, py0, py1, cx0, cx0 + s_ntx - 1, inv_tw);
+            }
             c0 = span.x;
             len = span.y >= span.x ? (unsigned)(span.y - span.x + 1) : 0u;
             rowbase = (unsigned)(vi.tile_base + ty * vi.tiles_x) * kDepthBins + (unsigned)s_bin;
@@ -229,23 +239,23 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
             if (j2 < tot2) {
                 const int tx = h0 + (int)(j2 - he);
                 const size_t bucket = hb + (size_t)tx * kDepthBins;
-                atomicAdd(a.tile_count + bucket, 1u);
-                if (a.occl) {
-                    const float4 g1 = s_og1[warp][ri & 31u];
-                    if (g1.w > 0.f) {
-                        const float4 g0 = s_og0[warp][ri & 31u];
-                        const OcclGauss g = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-                        const int ty = (int)(ri >> 8);
-                        const int x0 = tx * vb.tile_w, y0 = ty * vb.tile_h;
-                        const unsigned q = occl_units(g, (float)x0, (float)min(x0 + vb.tile_w - 1, vi.w - 1),
-                                                      (float)y0, (float)min(y0 + vb.tile_h - 1, vi.h - 1));
-                        if (q) atomicAdd(a.occl + bucket, q);
-                    }
+                if (!a.occl) {
+                    atomicAdd(a.tile_count + bucket, 1u);
+                } else {
+                    const float4 g0 = s_og0[warp][ri & 31u], g1 = s_og1[warp][ri & 31u];
+                    const OcclGauss g = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                    const int ty = (int)(ri >> 8);
+                    const int x0 = tx * vb.tile_w, y0 = ty * vb.tile_h;
+                    const unsigned q = occl_units(g, (float)x0, (float)min(x0 + vb.tile_w - 1, vi.w - 1),
+                                                  (float)y0, (float)min(y0 + vb.tile_h - 1, vi.h - 1));
+                    if (q) atomicAdd(a.occl + bucket, q);
                 }
             }
         }
     }
 }
+
+constexpr int kShStride = 257;  // shared-memory row of one SH coefficient over a CTA's 256 Gaussians
 
 template <int D>
 __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const __grid_constant__ ViewBatch vb) {
@@ -261,11 +271,23 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
     Activated A;
     bool ok = activate(ls, q, a.opacity_logits[g], A) && live;
     const float lo2 = log2f(A.opacity);  // per Gaussian, staged with every visible record
-    // Degree 0 keeps its colour in registers; higher degrees re-read their SH
-    // coefficients (L1-resident) in each view that sees the Gaussian rather
-    // than hold 3 (D + 1)^2 registers across the view loop.
+    // Degree 0 keeps its colour in registers. Higher degrees stage the CTA's SH
+    // coefficients in shared memory once (a coalesced copy of one contiguous block),
+    // and each view that sees a Gaussian reads them there: coefficient k of thread t
+    // sits at k * kShStride + t, so a warp's reads of one coefficient hit 32 banks.
     const float *cp = a.colors + (long long)g * NC * 3;
     float k0[3] = {cp[0], cp[1], cp[2]};
+    extern __shared__ float s_sh[];
+    if (D > 0) {
+        const long long g0 = (long long)blockIdx.x * blockDim.x;
+        const long long ng = a.n - g0 < (long long)blockDim.x ? a.n - g0 : (long long)blockDim.x;
+        const float *src = a.colors + g0 * NC * 3;
+        for (int e = threadIdx.x; e < (int)ng * NC * 3; e += blockDim.x) {
+            const int lt = e / (NC * 3), k = e - lt * (NC * 3);
+            s_sh[k * kShStride + lt] = __ldg(src + e);
+        }
+        __syncthreads();
+    }
 
     unsigned mask = 0;
     for (int v = 0; v < vb.n_views; ++v) {
@@ -331,7 +353,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
 #pragma unroll
                         for (int i = 1; i < NC; ++i) {
 #pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) c3[ch] += Y[i] * __ldg(cp + 3 * i + ch);
+                            for (int ch = 0; ch < 3; ++ch) c3[ch] += Y[i] * s_sh[(3 * i + ch) * kShStride + threadIdx.x];
                         }
 #pragma unroll
                         for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(c3[ch], 0.0f);
@@ -350,12 +372,14 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                     cbin = depth_bin(pz);
                     if (a.occl) {
                         // the blend's staged values (stage_record), and whether the
-                        // ellipse's inscribed disc is wide enough for a tile
+                        // ellipse on which alpha falls to kOcclAlpha (q = 2 ln(o / kOcclAlpha),
+                        // within the cover bound) has an inscribed disc wide enough for a tile
                         const StagedGauss sg = stage_record(R);
                         og = {sg.u, sg.v, sg.a, sg.b, sg.c, sg.thr, sg.lo2, 0.f};
                         const float ha = 0.5f * (R.a.z - R.b.x);
                         const float lmax = 0.5f * (R.a.z + R.b.x) + sqrtf(ha * ha + R.a.w * R.a.w);
-                        og.w = qc >= lmax * (float)a.tile_fit ? 1.f : 0.f;
+                        const float qa = fminf(qc, 2.0f * kLn2 * (lo2 - kOcclLog2Alpha) * 1.001f);
+                        og.w = qa > 0.f && qa >= lmax * (float)a.tile_fit ? 1.f : 0.f;
                     }
                 }
             }
@@ -654,16 +678,33 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
 
 }  // namespace
 
+// shared memory of the staged SH coefficients of degree D (none for degree 0)
+constexpr size_t sh_smem(int D) { return D == 0 ? 0 : (size_t)(D + 1) * (D + 1) * 3 * kShStride * sizeof(float); }
+
+template <int D>
+cudaError_t launch_project_d(const ProjectArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    // the opt-in above 48 KB is set once per device (setting it again is harmless)
+    static unsigned long long configured = 0;
+    int dev = 0;
+    if (sh_smem(D) > 0 && cudaGetDevice(&dev) == cudaSuccess && !(dev < 64 && ((configured >> dev) & 1ull))) {
+        cudaError_t e = cudaFuncSetAttribute(project_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sh_smem(D));
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured |= 1ull << dev;
+    }
+    project_kernel<D><<<grid, 256, sh_smem(D), s>>>(a, vb);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     int grid = (int)((a.n + 255) / 256);
     switch (a.sh_degree) {
-    case 0: project_kernel<0><<<grid, 256, 0, s>>>(a, vb); break;
-    case 1: project_kernel<1><<<grid, 256, 0, s>>>(a, vb); break;
-    case 2: project_kernel<2><<<grid, 256, 0, s>>>(a, vb); break;
-    default: project_kernel<3><<<grid, 256, 0, s>>>(a, vb); break;
+    case 0: return launch_project_d<0>(a, vb, grid, s);
+    case 1: return launch_project_d<1>(a, vb, grid, s);
+    case 2: return launch_project_d<2>(a, vb, grid, s);
+    default: return launch_project_d<3>(a, vb, grid, s);
     }
-    return cudaGetLastError();
 }
 
 int project_bwd_grid(long long n) { return (int)((n + 255) / 256); }

@@ -338,6 +338,11 @@ __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn
 // alpha_min), rounded down in fixed point, to its (tile, depth bin) bucket; the cut
 // is the first bin at which the tile's running sum reaches ln(1e4) plus a margin.
 constexpr float kOcclScale = 65536.0f;  // fixed-point units per nat
+// Pairs whose alpha bound is below this add nothing: leaving out part of the sum can
+// only move a cut later, and on scenes of large Gaussians these faint tile covers are
+// most of the pairs but little of the optical depth.
+constexpr float kOcclAlpha = 0.05f;
+constexpr float kOcclLog2Alpha = -4.3219280948873623f;  // log2(0.05)
 // ln(1e4) + 1e-3 in units: exp(-(ln(1e4) + 1e-3)) is below the FP32 constant 1e-4f
 constexpr unsigned kOcclThreshold = 603675u;
 
@@ -352,9 +357,39 @@ struct OcclGauss {
 // (the conic is positive definite), so over the rectangle its minimum is at a corner.
 // The FP32 error of the blend's evaluation at any pixel and of the evaluation here
 // at the corners is below 20 ulp of M = |a| dx^2 + |b dx dy| + |c| dy^2 taken at the
-// farthest extents; p is lowered by M 2^-18. alpha, -ln(1 - alpha) and the rounding
-// of each transmittance product (a factor of at most (1 + 2^-24)^2 per blended
-// Gaussian) are then covered by relative margins and one unit taken off each pair.
+// farthest extents; p is lowered by M 2^-18. The exponent l of alpha = 2^l is lowered
+// by 1e-5 and alpha (ex2.approx, relative error below 2^-22) by a factor 1 - 1e-5;
+// -log2(1 - alpha) (lg2.approx:
+// absolute error below 2^-22 on [0.5, 2], 2 ulp elsewhere; the rounding of 1 - alpha
+// moves it by less than 1e-5 for alpha <= 0.99) is lowered by 2e-5 and a factor
+// 1 - 1e-5. The rounding of each transmittance product (a factor of at most
+// (1 + 2^-24)^2 per blended Gaussian) is covered by one unit taken off each pair.
+// Tile columns of [tx0, tx1] whose pixel centres, on both edge rows py0 and py1 of
+// a tile row, lie where p >= T (a filter for occl_units, widened by a pixel: a tile
+// is inside the convex region exactly when its four corners are).
+__device__ __forceinline__ int2 strong_span(const OcclGauss &g, float T, int py0, int py1, int tx0, int tx1, int tw,
+                                            int w) {
+    float lo = -3.0e38f, hi = 3.0e38f;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float dy = (float)(k ? py1 : py0) - g.v;
+        const float B = g.b * dy, C = g.c * dy * dy - T;
+        const float disc = B * B - 4.0f * g.a * C;  // a < 0: p >= T between the roots
+        if (!(disc >= 0.f)) return make_int2(1, 0);
+        const float sq = sqrtf(disc), i2a = 0.5f / g.a;
+        const float r1 = (sq - B) * i2a, r2 = (-sq - B) * i2a;
+        lo = fmaxf(lo, g.u + fminf(r1, r2));
+        hi = fminf(hi, g.u + fmaxf(r1, r2));
+    }
+    lo -= 1.0f;
+    hi += 1.0f;
+    if (!(hi >= lo)) return make_int2(1, 0);
+    const float ftw = (float)tw;
+    const int first = max(tx0, (int)ceilf(fmaxf(lo, -1.0f) / ftw));
+    const int last = hi >= (float)(w - 1) ? tx1 : min(tx1, (int)floorf((hi - (float)(tw - 1)) / ftw));
+    return make_int2(first, last);
+}
+
 __device__ __forceinline__ unsigned occl_units(const OcclGauss &g, float x0, float x1, float y0, float y1) {
     const float dx0 = __fsub_rn(x0, g.u), dx1 = __fsub_rn(x1, g.u);
     const float dy0 = __fsub_rn(y0, g.v), dy1 = __fsub_rn(y1, g.v);
@@ -368,9 +403,12 @@ __device__ __forceinline__ unsigned occl_units(const OcclGauss &g, float x0, flo
     const float plo = pmin - M * 3.814697265625e-6f - 1e-6f;  // 2^-18
     if (!(plo >= g.thr)) return 0u;
     const float l = plo + g.lo2 - 1e-5f;
-    const float alpha = (l >= kClampL ? kAlphaMax : exp2f(l)) * (1.0f - 1e-5f);
-    const float od = -log1pf(-alpha) * (1.0f - 1e-5f);
-    const unsigned q = (unsigned)(od * kOcclScale);  // truncation rounds down
+    const float alpha = (l >= kClampL ? kAlphaMax : fast_exp2(l)) * (1.0f - 1e-5f);
+    if (alpha < kOcclAlpha) return 0u;
+    const float od2 = (-__log2f(1.0f - alpha) - 2e-5f) * (1.0f - 1e-5f);  // log2 units
+    const float q = od2 * (kLn2 * kOcclScale);
+    if (!(q >= 2.0f)) return 0u;
+    return (unsigned)q - 1u;  // truncation rounds down
     return q > 0u ? q - 1u : 0u;
 }
 
@@ -391,15 +429,16 @@ struct ProjectArgs {
 };
 cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s);
 
-// Per tile: the last depth bin its list keeps (255: all), and the counts of the
-// bins behind it set to 0 before the scan.
+// Per tile: the last depth bin its list keeps (255: all); per tile row and per view
+// the largest of these.
 struct CutArgs {
     const unsigned *occl;
-    unsigned *tile_count;
     unsigned char *cut;
+    unsigned *row_max;   // [tiles], at each row's first tile; zeroed before
+    unsigned *view_max;  // [views]; zeroed before
     long long n_tiles;
 };
-cudaError_t launch_cut(const CutArgs &a, cudaStream_t s);
+cudaError_t launch_cut(const CutArgs &a, const ViewBatch &vb, cudaStream_t s);
 
 struct ScanArgs {
     const unsigned *tile_count;  // per bucket
@@ -421,8 +460,12 @@ struct EmitArgs {
     unsigned long long key_capacity;
     const DevCounters *ctr;
     const unsigned char *cut;  // per tile last kept depth bin; null: keep all
+    const unsigned *row_max, *view_max;  // the cut's maxima (see CutArgs)
+    unsigned *tile_count;      // the count mode's bucket counts
 };
 cudaError_t launch_emit(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s);
+// The same enumeration counting the pairs in front of their tile's cut (a.cut set).
+cudaError_t launch_count(const EmitArgs &a, const ViewBatch &vb, cudaStream_t s);
 
 struct SortArgs {
     const unsigned *tile_start;  // bucket starts
