@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
 // Backward of the projection for every view of one Gaussian, accumulating
 // the parameter gradients in registers and writing each once.
 template <int D>
-__global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a, const __grid_constant__ ViewBatch vb) {
+__global__ void __launch_bounds__(256, 2) project_bwd_kernel(const ProjectBwdArgs a, const __grid_constant__ ViewBatch vb) {
     constexpr int NC = (D + 1) * (D + 1);
     __shared__ float s_tw[8][S3GS_MAX_VIEWS][6];
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,17 +407,31 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     Activated A;
     bool ok = activate(ls, q, a.opacity_logits[gg], A) && live;
-    float k[NC * 3];
-    const float *cp = a.colors + gg * NC * 3;
+    // Colour coefficients and their gradient: degree 0 in registers; higher degrees
+    // in shared memory (coefficient e of thread t at e * kShStride + t), staged and
+    // written back by the CTA as one contiguous block, so that 2 x 3 (D + 1)^2
+    // values per thread do not limit the kernel's occupancy.
+    extern __shared__ float s_dyn[];
+    float *s_k = s_dyn, *s_dk = s_dyn + NC * 3 * kShStride;
+    float k0[3] = {0.f, 0.f, 0.f}, dk0[3] = {0.f, 0.f, 0.f};
+    const long long g0 = (long long)blockIdx.x * blockDim.x;
+    const int ng = (int)(a.n - g0 < (long long)blockDim.x ? a.n - g0 : (long long)blockDim.x);
+    if (D == 0) {
+        const float *cp = a.colors + gg * 3;
+        k0[0] = cp[0]; k0[1] = cp[1]; k0[2] = cp[2];
+    } else {
+        const float *src = a.colors + g0 * NC * 3;
+        for (int e = threadIdx.x; e < ng * NC * 3; e += blockDim.x) {
+            const int lt = e / (NC * 3), kk = e - lt * (NC * 3);
+            s_k[kk * kShStride + lt] = __ldg(src + e);
+        }
 #pragma unroll
-    for (int i = 0; i < NC * 3; ++i) k[i] = cp[i];
+        for (int i = 0; i < NC * 3; ++i) s_dk[i * kShStride + threadIdx.x] = 0.f;
+    }
 
     float dmu[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // gradient w.r.t. the world covariance
     float dO = 0.f;
-    float dk[NC * 3];
-#pragma unroll
-    for (int i = 0; i < NC * 3; ++i) dk[i] = 0.f;
 
     // Views are processed in chunks whose 2D-gradient rows are all requested
     // before any is used, so their latencies overlap; the visibility mask says
@@ -549,7 +563,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
                 dO += gr[kGO];
                 // colour
                 if (D == 0) {
-                    dk[0] += gr[kGR]; dk[1] += gr[kGG]; dk[2] += gr[kGBl];
+                    dk0[0] += gr[kGR]; dk0[1] += gr[kGG]; dk0[2] += gr[kGBl];
                 } else {
                     float C[3];
                     cam_centre(T, C);
@@ -559,20 +573,23 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
                     float Y[16];
                     sh_basis<D>(hx, hy, hz, Y);
                     float gcol[3] = {gr[kGR], gr[kGG], gr[kGBl]};
+                    const float *kt = s_k + threadIdx.x;
+                    float *dkt = s_dk + threadIdx.x;
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
-                        float c = k[ch];
+                        float c = kt[ch * kShStride];
 #pragma unroll
-                        for (int i = 1; i < NC; ++i) c += Y[i] * k[3 * i + ch];
+                        for (int i = 1; i < NC; ++i) c += Y[i] * kt[(3 * i + ch) * kShStride];
                         if (!(c > 0.f)) gcol[ch] = 0.f;  // clamped at zero
                     }
                     float w[16];
 #pragma unroll
                     for (int i = 0; i < NC; ++i) {
-                        dk[3 * i] += Y[i] * gcol[0];
-                        dk[3 * i + 1] += Y[i] * gcol[1];
-                        dk[3 * i + 2] += Y[i] * gcol[2];
-                        w[i] = gcol[0] * k[3 * i] + gcol[1] * k[3 * i + 1] + gcol[2] * k[3 * i + 2];
+                        dkt[(3 * i) * kShStride] += Y[i] * gcol[0];
+                        dkt[(3 * i + 1) * kShStride] += Y[i] * gcol[1];
+                        dkt[(3 * i + 2) * kShStride] += Y[i] * gcol[2];
+                        w[i] = gcol[0] * kt[(3 * i) * kShStride] + gcol[1] * kt[(3 * i + 1) * kShStride] +
+                               gcol[2] * kt[(3 * i + 2) * kShStride];
                     }
                     float3 gh = sh_weighted_grad<D>(hx, hy, hz, w);
                     float dd = gh.x * hx + gh.y * hy + gh.z * hz;
@@ -649,10 +666,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
             *o = val;
         }
         if (a.d_opacity_logits) a.d_opacity_logits[g] = acc ? a.d_opacity_logits[g] + dol : dol;
-        if (a.d_colors) {
-            float *o = a.d_colors + g * NC * 3;
+        if (a.d_colors && D == 0) {
+            float *o = a.d_colors + g * 3;
 #pragma unroll
-            for (int i = 0; i < NC * 3; ++i) o[i] = acc ? o[i] + dk[i] : dk[i];
+            for (int i = 0; i < 3; ++i) o[i] = acc ? o[i] + dk0[i] : dk0[i];
         }
     } else if (live) {
         // invalid quaternion: the Gaussian is never rendered, its gradient is zero
@@ -662,11 +679,26 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
             if (a.d_log_scales) for (int i = 0; i < 3; ++i) a.d_log_scales[3 * g + i] = 0.f;
             if (a.d_quats) for (int i = 0; i < 4; ++i) a.d_quats[4 * g + i] = 0.f;
             if (a.d_opacity_logits) a.d_opacity_logits[g] = 0.f;
-            if (a.d_colors) for (int i = 0; i < NC * 3; ++i) a.d_colors[g * NC * 3 + i] = 0.f;
+            if (a.d_colors && D == 0) for (int i = 0; i < 3; ++i) a.d_colors[g * 3 + i] = 0.f;
         }
     }
 
     __syncthreads();
+    if (D > 0 && a.d_colors) {
+        // the CTA's colour gradients, one coalesced block; a Gaussian with an invalid
+        // quaternion gets zeros, or keeps its accumulated value
+        __shared__ unsigned char s_ok[256];
+        s_ok[threadIdx.x] = ok ? 1 : 0;
+        __syncthreads();
+        const bool acc = a.accumulate != 0;
+        float *dst = a.d_colors + g0 * NC * 3;
+        for (int e = threadIdx.x; e < ng * NC * 3; e += blockDim.x) {
+            const int lt = e / (NC * 3), kk = e - lt * (NC * 3);
+            if (acc && !s_ok[lt]) continue;
+            const float x = s_dk[kk * kShStride + lt];
+            dst[e] = acc ? dst[e] + x : x;
+        }
+    }
     // block partial of the twist, summed over warps in a fixed order
     for (int i = threadIdx.x; i < vb.n_views * 6; i += blockDim.x) {
         int v = i / 6, c = i % 6;
@@ -681,18 +713,34 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs a
 // shared memory of the staged SH coefficients of degree D (none for degree 0)
 constexpr size_t sh_smem(int D) { return D == 0 ? 0 : (size_t)(D + 1) * (D + 1) * 3 * kShStride * sizeof(float); }
 
+// Opts a kernel into `bytes` of dynamic shared memory (needed above 48 KB), once per
+// device; `configured` is the caller's per-kernel bit set of devices already done.
+template <class K>
+cudaError_t opt_in_smem(K kernel, size_t bytes, unsigned long long &configured) {
+    int dev = 0;
+    if (bytes == 0 || cudaGetDevice(&dev) != cudaSuccess) return cudaSuccess;
+    if (dev < 64 && ((configured >> dev) & 1ull)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev < 64) configured |= 1ull << dev;
+    return e;
+}
+
 template <int D>
 cudaError_t launch_project_d(const ProjectArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    // the opt-in above 48 KB is set once per device (setting it again is harmless)
     static unsigned long long configured = 0;
-    int dev = 0;
-    if (sh_smem(D) > 0 && cudaGetDevice(&dev) == cudaSuccess && !(dev < 64 && ((configured >> dev) & 1ull))) {
-        cudaError_t e = cudaFuncSetAttribute(project_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sh_smem(D));
-        if (e != cudaSuccess) return e;
-        if (dev < 64) configured |= 1ull << dev;
-    }
+    cudaError_t e = opt_in_smem(project_kernel<D>, sh_smem(D), configured);
+    if (e != cudaSuccess) return e;
     project_kernel<D><<<grid, 256, sh_smem(D), s>>>(a, vb);
+    return cudaGetLastError();
+}
+
+// the backward holds the coefficients and their gradients
+template <int D>
+cudaError_t launch_project_bwd_d(const ProjectBwdArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
+    static unsigned long long configured = 0;
+    cudaError_t e = opt_in_smem(project_bwd_kernel<D>, 2 * sh_smem(D), configured);
+    if (e != cudaSuccess) return e;
+    project_bwd_kernel<D><<<grid, 256, 2 * sh_smem(D), s>>>(a, vb);
     return cudaGetLastError();
 }
 
@@ -714,12 +762,11 @@ cudaError_t launch_project_bwd(const ProjectBwdArgs &a, const ViewBatch &vb, int
     if (grid_out) *grid_out = grid;
     if (a.n == 0) return cudaSuccess;
     switch (a.sh_degree) {
-    case 0: project_bwd_kernel<0><<<grid, 256, 0, s>>>(a, vb); break;
-    case 1: project_bwd_kernel<1><<<grid, 256, 0, s>>>(a, vb); break;
-    case 2: project_bwd_kernel<2><<<grid, 256, 0, s>>>(a, vb); break;
-    default: project_bwd_kernel<3><<<grid, 256, 0, s>>>(a, vb); break;
+    case 0: return launch_project_bwd_d<0>(a, vb, grid, s);
+    case 1: return launch_project_bwd_d<1>(a, vb, grid, s);
+    case 2: return launch_project_bwd_d<2>(a, vb, grid, s);
+    default: return launch_project_bwd_d<3>(a, vb, grid, s);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace s3gs
