@@ -46,7 +46,7 @@ TUNED_SCHEDULES = {
     3: {"blocks_per_sm": 12, "pixels_per_thread": 2, "bwd_pixels_per_thread": 4, "batch": 128, "full_lists": 1},
 }
 # blend schedule of the mapping-iteration row (run_mapping says how it was chosen)
-MAPPING_SCHEDULE = {"blocks_per_sm": 8, "pixels_per_thread": 2, "bwd_pixels_per_thread": 2}
+MAPPING_SCHEDULE = {"blocks_per_sm": 8, "pixels_per_thread": 2, "bwd_pixels_per_thread": 2, "full_lists": 1}
 
 
 def parse():
