@@ -662,22 +662,12 @@ size_t bwd_smem(int batch, int n_warps, bool det) {
     return s;
 }
 
-// Raise a kernel's dynamic shared-memory limit only when a larger size is first
-// needed, so that steady-state calls (and stream capture) issue nothing but launches.
-template <class K>
-cudaError_t ensure_smem(K kernel, size_t bytes, int *cached) {
-    if ((int)bytes <= *cached) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) *cached = (int)bytes;
-    return e;
-}
-
 template <int TW, int TH, int P, bool C>
 cudaError_t fwd_impl3(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    static int cached = 0;
+    static SmemOptIn st;
     const size_t sm = fwd_smem(a.batch);
     auto k = blend_fwd_kernel<TW, TH, P, C>;
-    cudaError_t e = ensure_smem(k, sm, &cached);
+    cudaError_t e = opt_in_smem(k, sm, st);
     if (e != cudaSuccess) return e;
     k<<<grid, TW * TH / P, sm, s>>>(a, vb);
     return cudaGetLastError();
@@ -690,10 +680,10 @@ cudaError_t fwd_impl2(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStr
 
 template <int TW, int TH, int P, bool R, bool D, bool C, bool G = false>
 cudaError_t bwd_impl4(const BlendArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    static int cached = 0;
+    static SmemOptIn st;
     const size_t sm = bwd_smem(a.batch, TW * TH / P / 32, D);
     auto k = blend_bwd_kernel<TW, TH, P, R, D, C, G>;
-    cudaError_t e = ensure_smem(k, sm, &cached);
+    cudaError_t e = opt_in_smem(k, sm, st);
     if (e != cudaSuccess) return e;
     k<<<grid, TW * TH / P, sm, s>>>(a, vb);
     return cudaGetLastError();

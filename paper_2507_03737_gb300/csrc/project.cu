@@ -713,22 +713,10 @@ __global__ void __launch_bounds__(256, 2) project_bwd_kernel(const ProjectBwdArg
 // shared memory of the staged SH coefficients of degree D (none for degree 0)
 constexpr size_t sh_smem(int D) { return D == 0 ? 0 : (size_t)(D + 1) * (D + 1) * 3 * kShStride * sizeof(float); }
 
-// Opts a kernel into `bytes` of dynamic shared memory (needed above 48 KB), once per
-// device; `configured` is the caller's per-kernel bit set of devices already done.
-template <class K>
-cudaError_t opt_in_smem(K kernel, size_t bytes, unsigned long long &configured) {
-    int dev = 0;
-    if (bytes == 0 || cudaGetDevice(&dev) != cudaSuccess) return cudaSuccess;
-    if (dev < 64 && ((configured >> dev) & 1ull)) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess && dev < 64) configured |= 1ull << dev;
-    return e;
-}
-
 template <int D>
 cudaError_t launch_project_d(const ProjectArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    static unsigned long long configured = 0;
-    cudaError_t e = opt_in_smem(project_kernel<D>, sh_smem(D), configured);
+    static SmemOptIn st;
+    cudaError_t e = opt_in_smem(project_kernel<D>, sh_smem(D), st);
     if (e != cudaSuccess) return e;
     project_kernel<D><<<grid, 256, sh_smem(D), s>>>(a, vb);
     return cudaGetLastError();
@@ -737,8 +725,8 @@ cudaError_t launch_project_d(const ProjectArgs &a, const ViewBatch &vb, int grid
 // the backward holds the coefficients and their gradients
 template <int D>
 cudaError_t launch_project_bwd_d(const ProjectBwdArgs &a, const ViewBatch &vb, int grid, cudaStream_t s) {
-    static unsigned long long configured = 0;
-    cudaError_t e = opt_in_smem(project_bwd_kernel<D>, 2 * sh_smem(D), configured);
+    static SmemOptIn st;
+    cudaError_t e = opt_in_smem(project_bwd_kernel<D>, 2 * sh_smem(D), st);
     if (e != cudaSuccess) return e;
     project_bwd_kernel<D><<<grid, 256, 2 * sh_smem(D), s>>>(a, vb);
     return cudaGetLastError();

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/s3gs.h"
 
 namespace s3gs {
@@ -410,6 +412,30 @@ __device__ __forceinline__ unsigned occl_units(const OcclGauss &g, float x0, flo
     if (!(q >= 2.0f)) return 0u;
     return (unsigned)q - 1u;  // truncation rounds down
     return q > 0u ? q - 1u : 0u;
+}
+
+// ---- dynamic shared memory above the default limit ----
+// A kernel needs cudaFuncAttributeMaxDynamicSharedMemorySize raised, per device, before
+// it is launched with more than 48 KB of dynamic shared memory. Each launcher keeps one
+// SmemOptIn per kernel; the attribute is raised only when a larger size than before is
+// first needed on the current device, so steady-state calls (and stream capture) issue
+// nothing but the launch.
+struct SmemOptIn {
+    std::mutex mu;
+    size_t bytes[64] = {};
+};
+
+template <class K>
+cudaError_t opt_in_smem(K kernel, size_t bytes, SmemOptIn &st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(st.mu);
+    if (st.bytes[dev] >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) st.bytes[dev] = bytes;
+    return e;
 }
 
 // ---- launch wrappers (one per translation unit) ----

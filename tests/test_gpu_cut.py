@@ -134,3 +134,58 @@ def test_cut_with_recompute_and_persistent_grid(R):
         res[fl] = R.backward_np(ups, len(sc.cameras))
     for k in res[1]:
         assert np.array_equal(res[1][k].view(np.uint32), res[0][k].view(np.uint32)), k
+
+
+def _wall_ragged():
+    """The opaque wall seen by uneven views whose border tiles are partial."""
+    sc = _case("opaque_wall")
+    sc.cameras = [scenes.camera(77, 45, 70.0, 70.0, 38.0, 22.0), scenes.camera(33, 70, 40.0, 40.0, 16.5, 35.0),
+                  scenes.camera(1, 1, 10.0, 10.0, 0.5, 0.5), scenes.camera(161, 7, 120.0, 120.0, 80.0, 3.0)]
+    return sc
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (16, 8), (8, 8), (32, 8)])
+def test_cut_every_tile_shape_on_ragged_views(R, tile):
+    """Each tile shape (a different inradius filter and partial border tiles)."""
+    sc = _wall_ragged()
+    tw, th = tile
+    full, fkeys, fvals, franges = _lists(R, sc, full_lists=1, tile_w=tw, tile_h=th)
+    cut, keys, vals, ranges = _lists(R, sc, tile_w=tw, tile_h=th)
+    n_cut_tiles = _check_prefix(keys, vals, ranges, fkeys, fvals, franges)
+    for k in full:
+        assert np.array_equal(full[k].view(np.uint32), cut[k].view(np.uint32)), k
+    print(f"CUT ragged {tw}x{th}: kept {keys.size} of {fkeys.size}; tiles cut {n_cut_tiles} of {ranges.size - 1}")
+    assert n_cut_tiles > 0
+
+
+def test_cut_behind_three_opaque_layers(R):
+    """Three wide, nearly opaque Gaussians in one depth bin in front of 5,000 small ones:
+    over every tile each has alpha >= 0.98, so three of them stop every pixel (T <= 1e-5)
+    and every tile's list must end with them, with nothing else listed."""
+    rng = np.random.default_rng(4)
+    n = 5000
+    front = np.array([[0.0, 0.0, 2.0], [0.0, 0.0, 2.02], [0.0, 0.0, 2.04]])
+    back = np.stack([rng.uniform(-2, 2, n), rng.uniform(-2, 2, n), rng.uniform(3, 8, n)], 1)
+    sc = scenes.random_gaussians(rng, np.concatenate([front, back]), 0)
+    sc.log_scales[:3] = np.log(np.array([10.0, 10.0, 0.05])).astype(np.float32)
+    sc.quats[:3] = np.array([1, 0, 0, 0], np.float32)
+    sc.opacity_logits[:3] = 8.0
+    sc.cameras = [scenes.camera(96, 64, 60.0, 60.0, 48.0, 32.0)]
+    full, fkeys, fvals, franges = _lists(R, sc, full_lists=1)
+    cut, keys, vals, ranges = _lists(R, sc)
+    _check_prefix(keys, vals, ranges, fkeys, fvals, franges)
+    for k in full:
+        assert np.array_equal(full[k].view(np.uint32), cut[k].view(np.uint32)), k
+    assert np.all(np.diff(ranges) == 3) and set(np.unique(vals)) == {0, 1, 2}
+    assert fkeys.size > 10 * keys.size
+
+
+def test_cut_pose_only_backward(R):
+    """The geometry-only (tracking) backward reads the same cut lists."""
+    sc = _wall_ragged()
+    ups = upstream(sc.cameras, 9)
+    res = {}
+    for fl in (1, 0):
+        _lists(R, sc, full_lists=fl, deterministic=1)
+        res[fl] = R.backward_np(ups, len(sc.cameras), want=("twist",))
+    assert np.array_equal(res[1]["twist"].view(np.uint32), res[0]["twist"].view(np.uint32))
