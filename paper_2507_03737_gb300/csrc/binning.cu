@@ -612,6 +612,49 @@ __device__ __forceinline__ unsigned sub_bin(unsigned zb, const unsigned short *s
 // merged into segments, are sorted: up to 128 keys by single warps in
 // registers, longer ones by the whole block. A staged tile is stored back with
 // one coalesced store.
+// Fast path for a tile whose buckets all hold at most 32 keys (the common case when
+// Gaussians are small): warp w takes buckets 32w .. 32w + 31 and walks them in windows
+// of whole buckets of at most 32 keys. Keys of an earlier bucket precede those of a
+// later one (the bucket is the depth bin, a monotone function of the depth bits that
+// lead the key), so a key's place is its bucket's first place in the window plus the
+// number of smaller keys in its bucket; the lanes of a bucket are found with match_any
+// and compared with shuffles, one round per key of the largest bucket in the window.
+// Keys go from the emission buffer to the sorted list directly.
+__device__ __forceinline__ unsigned key_bin(unsigned long long key) {
+    const int b = (int)((unsigned)(key >> 32) >> 19) - 1993;  // depth_bin of the key's depth bits
+    return b < 0 ? 0u : (b > kDepthBins - 1 ? (unsigned)(kDepthBins - 1) : (unsigned)b);
+}
+
+__device__ void sort_small_buckets(const SortArgs &a, const unsigned *bs, unsigned base) {
+    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const unsigned long long *in = a.keys_in + base;
+    unsigned long long *out = a.keys + base;
+    const unsigned bnd = bs[32 * w + lane] - base;  // start of bucket 32 w + lane
+    const unsigned endw = bs[32 * w + 32] - base;
+    unsigned w0 = __shfl_sync(0xffffffffu, bnd, 0);
+    while (w0 < endw) {
+        // the window ends at the last bucket boundary within 32 keys (every bucket is
+        // at most 32 keys long, so there is one beyond w0)
+        const unsigned lim = w0 + 32u;
+        const unsigned w1 = max(__reduce_max_sync(0xffffffffu, (bnd > w0 && bnd <= lim) ? bnd : 0u),
+                                endw <= lim ? endw : 0u);
+        const unsigned i = w0 + lane;
+        const bool act = i < w1;
+        const unsigned long long key = act ? in[i] : kInfKey;
+        const unsigned peers = __match_any_sync(0xffffffffu, act ? key_bin(key) : 0x10000u + lane);
+        const unsigned first = __ffs(peers) - 1, size = __popc(peers);
+        const unsigned rounds = __reduce_max_sync(0xffffffffu, act ? size : 0u);
+        unsigned rank = 0;
+        for (unsigned d = 0; d < rounds; ++d) {
+            const unsigned long long y = __shfl_sync(0xffffffffu, key, (first + d) & 31u);
+            rank += (d < size && y < key) ? 1u : 0u;
+        }
+        if (act) out[w0 + first + rank] = key;
+        if (w1 <= w0) break;  // cannot happen: the caller checked every bucket's length
+        w0 = w1;
+    }
+}
+
 __global__ void __launch_bounds__(kSortThreads, 5) tile_sort_kernel(const SortArgs a) {
     __shared__ unsigned long long s_k[kSortCap];
     __shared__ unsigned s_start[kDepthBins + 1];
@@ -631,6 +674,10 @@ __global__ void __launch_bounds__(kSortThreads, 5) tile_sort_kernel(const SortAr
     }
     static_assert(kSortThreads == kDepthBins, "one thread per bucket");
     const unsigned b = threadIdx.x;
+    if (!__syncthreads_or(bs[b + 1] - bs[b] > 32u)) {
+        sort_small_buckets(a, bs, base);
+        return;
+    }
     s_start[b] = bs[b] - base;
     if (b == 0) s_start[kDepthBins] = n_tile;
     __syncthreads();
