@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const ScanArgs a) {
 // cut, before the scan), counting only the pairs in front of their tile's cut. A
 // record behind its view's largest cut is skipped whole, a row behind the row's
 // largest cut costs no level-2 work, and each pair is checked against its tile's cut.
+constexpr unsigned kRowSeqMax = 4;  // longest tile row a lane expands by itself
+
 template <bool COUNT>
 __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __grid_constant__ ViewBatch vb) {
     __shared__ unsigned s_incl[8][32], s_excl[8][32], s_t0[8][32], s_ntx[8][32], s_orig[8][32];
@@ -202,6 +204,30 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
                 len = span.y >= span.x ? (unsigned)(span.y - span.x + 1) : 0u;
                 rkey = s_key[warp][src];
             }
+        }
+        const unsigned maxlen = __reduce_max_sync(0xffffffffu, len);
+        if (maxlen <= kRowSeqMax) {
+            // short rows (small Gaussians): each lane takes its own row's tiles, four
+            // at a time, rather than spreading the round's tiles over the warp
+            for (unsigned q0 = 0; q0 < maxlen; q0 += 4) {
+                unsigned pos[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned q = q0 + (unsigned)u;
+                    const unsigned bucket = rowbase + (unsigned)(c0 + (int)q) * kDepthBins;
+                    pos[u] = 0xffffffffu;
+                    if (q < len && (!a.cut || (bucket & (kDepthBins - 1)) <= a.cut[bucket / kDepthBins])) {
+                        if (COUNT) atomicAdd(a.tile_count + bucket, 1u);
+                        else pos[u] = atomicAdd(a.cursor + bucket, 1u);
+                    }
+                }
+                if (!COUNT) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (pos[u] < a.key_capacity) a.keys[pos[u]] = rkey;
+                }
+            }
+            continue;
         }
         const unsigned incl2 = warp_incl_scan(len);
         const unsigned tot2 = __shfl_sync(0xffffffffu, incl2, 31);
