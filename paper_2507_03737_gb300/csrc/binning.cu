@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const ScanArgs a) {
 // cut, before the scan), counting only the pairs in front of their tile's cut. A
 // record behind its view's largest cut is skipped whole, a row behind the row's
 // largest cut costs no level-2 work, and each pair is checked against its tile's cut.
-constexpr unsigned kRowSeqMax = 4;  // longest tile row a lane expands by itself
+constexpr unsigned kRowSeqMax = 16;  // longest tile row a lane expands by itself (a round of longer rows is spread over the warp)
 
 template <bool COUNT>
 __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __grid_constant__ ViewBatch vb) {
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const EmitArgs a, const __gri
         }
         const unsigned maxlen = __reduce_max_sync(0xffffffffu, len);
         if (maxlen <= kRowSeqMax) {
-            // short rows (small Gaussians): each lane takes its own row's tiles, four
+            // short rows: each lane takes its own row's tiles, four
             // at a time, rather than spreading the round's tiles over the warp
             for (unsigned q0 = 0; q0 < maxlen; q0 += 4) {
                 unsigned pos[4];

@@ -226,7 +226,7 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
             len = span.y >= span.x ? (unsigned)(span.y - span.x + 1) : 0u;
             rowbase = (unsigned)(vi.tile_base + ty * vi.tiles_x) * kDepthBins + (unsigned)s_bin;
         }
-        if (!a.occl && __reduce_max_sync(0xffffffffu, len) <= 4u) {
+        if (!a.occl && __reduce_max_sync(0xffffffffu, len) <= 16u) {
             // short rows (small Gaussians): each lane counts its own row's tiles
             for (unsigned q = 0; q < len; ++q) atomicAdd(a.tile_count + rowbase + (size_t)(c0 + (int)q) * kDepthBins, 1u);
             continue;
