@@ -72,7 +72,10 @@ struct s3gs_state {
     DevBuf<unsigned> tile_count, tile_start, cursor, order, scan_part;
     DevBuf<unsigned> occl;        // per bucket optical depth lower bound (occlusion cut)
     DevBuf<unsigned char> cut;    // per tile last listed depth bin
-    DevBuf<unsigned> cut_max;     // [tiles] row maxima of the cut (at row starts), then [32] view maxima
+    DevBuf<unsigned> cut_max;     // [tiles] row maxima of the cut (at row starts)
+    DevBuf<unsigned> cut_view;    // [32] view maxima of the cut; the next forward's hint
+    const void *cut_hint_for = nullptr;  // cut buffer whose contents are a valid hint ...
+    long long cut_hint_tiles = -1;       // ... for a view batch of this many tiles
     DevBuf<unsigned long long> keys;       // tile-sorted duplicate list
     DevBuf<unsigned long long> keys_emit;  // emission order, read by the tile sort
     DevBuf<float> det_partial;
@@ -245,7 +248,8 @@ s3gs_status ensure_forward_buffers(s3gs_ctx *ctx, s3gs_state *st, long long n_re
     if ((r = grow(ctx, st->scan_part, (n_buckets + 4095) / 4096 + 2, s, "scan_part")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->occl, n_buckets + 1, s, "occlusion")) != S3GS_OK) return r;
     if ((r = grow(ctx, st->cut, n_tiles + 16, s, "cut")) != S3GS_OK) return r;
-    if ((r = grow(ctx, st->cut_max, n_tiles + S3GS_MAX_VIEWS, s, "cut_max")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->cut_max, n_tiles + 16, s, "cut_max")) != S3GS_OK) return r;
+    if ((r = grow(ctx, st->cut_view, S3GS_MAX_VIEWS, s, "cut_view")) != S3GS_OK) return r;
     if (store) {
         if ((r = grow(ctx, st->T_final, n_pix, s, "T_final")) != S3GS_OK) return r;
         if ((r = grow(ctx, st->n_last, n_pix, s, "n_last")) != S3GS_OK) return r;
@@ -379,7 +383,7 @@ void s3gs_state_destroy(s3gs_state *st) {
                     st->tile_start.p, st->cursor.p,    st->order.p,     st->scan_part.p,   st->bucket,
                     st->keys.p,      st->keys_emit.p, st->det_partial.p, st->T_final.p,   st->n_last.p,
                     st->twist_part.p, st->loss_part.p, st->occl.p,   st->cut.p,       st->cut_max.p,
-                    st->ctr};
+                    st->cut_view.p,  st->ctr};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (st->ctr_host) cudaFreeHost(st->ctr_host);
@@ -455,7 +459,14 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     const bool cut = !opt.full_lists;
     if (cut) {
         CK(cudaMemsetAsync(st->occl.p, 0, (size_t)NBK * sizeof(unsigned), s), "memset occlusion");
-        CK(cudaMemsetAsync(st->cut_max.p, 0, (size_t)(T + S3GS_MAX_VIEWS) * sizeof(unsigned), s), "memset cut maxima");
+        CK(cudaMemsetAsync(st->cut_max.p, 0, (size_t)T * sizeof(unsigned), s), "memset cut row maxima");
+        if (st->cut_hint_for != (const void *)st->cut.p || st->cut_hint_tiles != T) {
+            // no previous cut of this layout: hints that exclude nothing
+            CK(cudaMemsetAsync(st->cut.p, 0xff, (size_t)T, s), "init cut hint");
+            CK(cudaMemsetAsync(st->cut_view.p, 0xff, S3GS_MAX_VIEWS * sizeof(unsigned), s), "init view hint");
+            st->cut_hint_for = st->cut.p;
+            st->cut_hint_tiles = T;
+        }
     }
 
     ProjectArgs pa;
@@ -465,6 +476,7 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     pa.Tdev = T_cw_device;
     pa.rec = st->rec.p; pa.ext = st->ext.p; pa.vis_mask = st->vis_mask.p; pa.tile_count = st->tile_count.p;
     pa.occl = cut ? st->occl.p : nullptr;
+    pa.cut_hint = st->cut.p; pa.view_hint = st->cut_view.p;
     {
         const int m = (opt.tile_w < opt.tile_h ? opt.tile_w : opt.tile_h) - 1;
         pa.tile_fit = m * m / 4;
@@ -473,15 +485,17 @@ s3gs_status s3gs_render_fwd(s3gs_ctx *ctx, s3gs_state *st, const s3gs_gaussians 
     ea.rec = st->rec.p; ea.ext = st->ext.p; ea.n = n; ea.cursor = st->cursor.p; ea.keys = nullptr;
     ea.key_capacity = 0; ea.ctr = st->ctr; ea.tile_count = st->tile_count.p;
     ea.cut = cut ? st->cut.p : nullptr;
-    ea.row_max = st->cut_max.p; ea.view_max = st->cut_max.p + T;
+    ea.row_max = st->cut_max.p; ea.view_max = st->cut_view.p;
     {
         // with the cut: projection and optical depths, the cut, then the bucket counts
         StageTimer tm(ctx, kStProject, s);
         CK(launch_project(pa, vb, s), "project");
         if (cut) {
+            // the projection has read the hints; the cut kernel now overwrites them
+            CK(cudaMemsetAsync(st->cut_view.p, 0, S3GS_MAX_VIEWS * sizeof(unsigned), s), "memset cut view maxima");
             CutArgs ca;
             ca.occl = st->occl.p; ca.cut = st->cut.p; ca.n_tiles = T;
-            ca.row_max = st->cut_max.p; ca.view_max = st->cut_max.p + T;
+            ca.row_max = st->cut_max.p; ca.view_max = st->cut_view.p;
             CK(launch_cut(ca, vb, s), "cut");
             CK(launch_count(ea, vb, s), "count");
         }

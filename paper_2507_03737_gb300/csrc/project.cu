@@ -246,7 +246,7 @@ __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const Vie
                 const size_t bucket = hb + (size_t)tx * kDepthBins;
                 if (!a.occl) {
                     atomicAdd(a.tile_count + bucket, 1u);
-                } else {
+                } else if ((bucket & (kDepthBins - 1)) <= a.cut_hint[bucket / kDepthBins] + kHintSlack) {
                     const float4 g0 = s_og0[warp][ri & 31u], g1 = s_og1[warp][ri & 31u];
                     const OcclGauss g = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
                     const int ty = (int)(ri >> 8);
@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                         const float ha = 0.5f * (R.a.z - R.b.x);
                         const float lmax = 0.5f * (R.a.z + R.b.x) + sqrtf(ha * ha + R.a.w * R.a.w);
                         const float qa = fminf(qc, 2.0f * kLn2 * (lo2 - kOcclLog2Alpha) * 1.001f);
-                        og.w = qa > 0.f && qa >= lmax * (float)a.tile_fit ? 1.f : 0.f;
+                        og.w = qa > 0.f && qa >= lmax * (float)a.tile_fit &&
+                                       (unsigned)cbin <= a.view_hint[v] + kHintSlack ? 1.f : 0.f;
                     }
                 }
             }

@@ -340,6 +340,7 @@ __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn
 // alpha_min), rounded down in fixed point, to its (tile, depth bin) bucket; the cut
 // is the first bin at which the tile's running sum reaches ln(1e4) plus a margin.
 constexpr float kOcclScale = 65536.0f;  // fixed-point units per nat
+constexpr unsigned kHintSlack = 4;      // depth bins (a quarter octave) beyond a cut hint
 // Pairs whose alpha bound is below this add nothing: leaving out part of the sum can
 // only move a cut later, and on scenes of large Gaussians these faint tile covers are
 // most of the pairs but little of the optical depth.
@@ -452,6 +453,15 @@ struct ProjectArgs {
     unsigned *tile_count;
     unsigned *occl;      // per bucket optical depth lower bound (see occl_units); null: no cut
     int tile_fit;        // (min(tile_w, tile_h) - 1)^2 / 4: squared inradius a tile needs
+    // Hints: the previous forward's cut per tile and its largest value per view (all 255
+    // when there is none). Pairs behind the hint add no optical depth. Whatever the hint,
+    // the sums of the bins up to it are complete, so a tile whose sum reaches the threshold
+    // there gets the same cut as without a hint, and one whose sum does not keeps its
+    // whole list (the cut search then finds no bin): the hint can only lose culling.
+    const unsigned char *cut_hint;
+    const unsigned *view_hint;
+    // (pairs up to kHintSlack bins behind the hint still add, so that a cut that moves
+    // back a little between two forwards is still found)
 };
 cudaError_t launch_project(const ProjectArgs &a, const ViewBatch &vb, cudaStream_t s);
 

@@ -189,3 +189,38 @@ def test_cut_pose_only_backward(R):
         _lists(R, sc, full_lists=fl, deterministic=1)
         res[fl] = R.backward_np(ups, len(sc.cameras), want=("twist",))
     assert np.array_equal(res[1]["twist"].view(np.uint32), res[0]["twist"].view(np.uint32))
+
+
+def _moved_wall(dz):
+    sc = _case("opaque_wall")
+    sc.means = sc.means.copy()
+    sc.means[:, 2] += np.float32(dz)
+    return sc
+
+
+def test_cut_hints_from_previous_forwards(R):
+    """A forward with the cut takes the previous forward's cut as a hint (pairs behind it
+    add no optical depth). Whatever the hint, the result must equal the full lists: the
+    same scene again (a hint that matches), then the wall moved back by 2 m (a hint that
+    ends too early: those tiles keep more), then moved forward again (a hint that ends
+    late), and the first scene once more."""
+    seq = [("same", _case("opaque_wall")), ("same again", _case("opaque_wall")),
+           ("wall 2 m back", _moved_wall(2.0)), ("wall 1 m forward", _moved_wall(-1.0)),
+           ("first again", _case("opaque_wall"))]
+    kept = []
+    for name, sc in seq:
+        full, fkeys, fvals, franges = _lists(R, sc, full_lists=1)
+        # full lists leave the hint alone; run the cut twice so the second sees this
+        # scene's own cut, after a first run that sees the previous scene's
+        for rep in range(2):
+            cut, keys, vals, ranges = _lists(R, sc)
+            _check_prefix(keys, vals, ranges, fkeys, fvals, franges)
+            for k in full:
+                assert np.array_equal(full[k].view(np.uint32), cut[k].view(np.uint32)), (name, rep, k)
+            kept.append(keys.size)
+        print(f"CUT hint {name}: kept {kept[-2]} then {kept[-1]} of {fkeys.size}")
+    # a tile's own previous cut as the hint gives that cut again (the sums up to it are
+    # complete), and the same as no hint; a stale hint can only keep more
+    own = kept[1::2]
+    assert own[0] == own[1] == own[4]
+    assert all(kept[2 * i + 1] <= kept[2 * i] for i in range(len(seq)))
