@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs a, const
                         const float lmax = 0.5f * (R.a.z + R.b.x) + sqrtf(ha * ha + R.a.w * R.a.w);
                         const float qa = fminf(qc, 2.0f * kLn2 * (lo2 - kOcclLog2Alpha) * 1.001f);
                         og.w = qa > 0.f && qa >= lmax * (float)a.tile_fit &&
-                                       (unsigned)cbin <= a.view_hint[v] + kHintSlack ? 1.f : 0.f;
+                                       (unsigned)cbin <= min(a.view_hint[v], 255u) + kHintSlack ? 1.f : 0.f;
                     }
                 }
             }
