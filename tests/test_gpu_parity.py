@@ -178,10 +178,17 @@ def test_batched_equals_per_view(R):
 
 
 def test_persistent_and_recompute_and_det(R):
+    """Every schedule against the oracle, and against the default schedule (outputs
+    bitwise, gradients to 1e-5; deterministic mode bitwise)."""
     sc = scenes.tiny_scene(9, n=600, width=80, height=60, n_views=2, scale=0.15)
-    ups = upstream(sc.cameras, 5)
+    ref = O.render_fwd(sc)
+    ups = upstream(sc.cameras, 5, pixel_mask(ref))
+    gref = O.render_bwd(sc, **ups)
     base = R.render_np(sc)
+    # a dense scene (600 Gaussians over 80 x 60 pixels): 26 of 9,600 pixels lie in the band
+    compare_forward(base, ref, sc.cameras, name="schedules default", max_excluded=0.004)
     g0 = R.backward_np(ups, 2)
+    compare_grads(g0, gref)
     outs = {}
     for name, kw in (("persistent", dict(blocks_per_sm=2)), ("recompute", dict(recompute=1)),
                      ("ppt1", dict(pixels_per_thread=1, bwd_pixels_per_thread=1)),
@@ -193,6 +200,7 @@ def test_persistent_and_recompute_and_det(R):
         for k in base:
             np.testing.assert_array_equal(out[k], base[k], err_msg=f"{name} {k}")
         outs[name] = R.backward_np(ups, 2)
+        compare_grads(outs[name], gref)
         for k in g0:
             assert rel_l2(outs[name][k], g0[k]) < 1e-5, (name, k)
     for k in g0:  # deterministic mode is bitwise reproducible, whatever the schedule
@@ -205,8 +213,14 @@ def test_persistent_and_recompute_and_det(R):
 
 
 def test_batch_size_and_tile_do_not_change_forward(R):
+    """Each tile shape, batch size and pixels-per-thread setting: the forward bitwise equal
+    to the default's, which matches the oracle, and the gradients against the oracle."""
     sc = scenes.config_scene(1)
+    ref = O.render_fwd(sc)
+    ups = upstream(sc.cameras, 8, pixel_mask(ref))
+    gref = O.render_bwd(sc, **ups)
     base = R.render_np(sc)
+    compare_forward(base, ref, sc.cameras, name="tiles default")
     for kw in (dict(batch=32), dict(batch=1024), dict(tile_w=8, tile_h=8, batch=17, bwd_pixels_per_thread=2),
                dict(tile_w=32, tile_h=8),
                dict(pixels_per_thread=1), dict(pixels_per_thread=4, batch=100),
@@ -215,6 +229,7 @@ def test_batch_size_and_tile_do_not_change_forward(R):
         out = R.render_np(sc, options=_opts(**kw))
         for k in base:
             np.testing.assert_array_equal(out[k], base[k], err_msg=str(kw))
+        compare_grads(R.backward_np(ups, 1), gref)
 
 
 def test_background_colour(R):
