@@ -410,7 +410,7 @@ def test_autograd_function_and_pose_gradient(R):
         rgb, depth, pm, alpha = render(R, p, [off], twist=tw)
         loss = (rgb - target[0]).abs().mean()
         loss.backward()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
         g = tw.grad.detach().cpu().numpy()[0].astype(np.float64)
         off = dict(off, T_cw=apply_twist(off["T_cw"], -2e-3 * g / max(np.linalg.norm(g), 1e-12)))
     assert losses[-1] < losses[0]
