@@ -121,7 +121,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const ScanArgs a) {
 // the round's covered tiles and every lane emits one key per sub-round. All lanes
 // stay busy whatever the mix of visible, culled, small and large records, and
 // only covered tiles cost a cursor atomic. Four sub-rounds of cursor atomics
-// are issued before their results are consumed.
+// are issued before their results are consumed. A round whose rows are all short
+// (at most kRowSeqMax tiles, the common case for small Gaussians) skips level 2:
+// each lane expands its own row, four tiles at a time.
 //
 // With the occlusion cut the same enumeration first runs in COUNT mode (after the
 // cut, before the scan), counting only the pairs in front of their tile's cut. A

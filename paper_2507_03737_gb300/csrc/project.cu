@@ -177,8 +177,9 @@ __device__ __forceinline__ float view_coord(const float *r, const float m[3], fl
 // fetches the record's cover ellipse with shuffles and computes the row's span of
 // covered tile columns (row_span). Level 2: a second scan numbers the round's
 // covered tiles, and in each sub-round every lane counts one. All lanes stay busy
-// whatever the mix of record sizes, and only covered tiles cost a count. With the
-// occlusion cut on, the bucket counts are made later (after the cut) and this pass
+// whatever the mix of record sizes, and only covered tiles cost a count (a round
+// whose rows are all at most 16 tiles long skips level 2: each lane counts its own
+// row). With the occlusion cut on, the bucket counts are made later (after the cut) and this pass
 // takes only the records that can hold a whole tile: each of their pairs adds its
 // optical depth bound over the tile to the bucket (occl_units).
 __device__ __forceinline__ void count_cover_warp(const ProjectArgs &a, const ViewBatch &vb, const ViewInfo &vi,
